@@ -1,0 +1,876 @@
+/*
+ * mpm_oracle.c -- plain, slow FP64 CPU oracle of the MLS-MPM substep and of its
+ * reverse-mode adjoint.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may load this file or
+ * the library built from it: it is used by tests/, by the smoke check and by the
+ * timed CPU baseline of bench.py.  It shares no code, header or table with the
+ * CUDA library; both only consume the same seeded inputs.
+ *
+ * What it follows (FastPhysGS, arXiv 2602.01723):
+ *   - substep order: stress from F, P2G, grid update, G2P, plasticity
+ *     (Algorithm 1, Stage 1; §3.2 "Material Point Method");
+ *   - P2G with the MLS stress term inside the affine momentum
+ *     (§4.2, momentum-exchange equation; App. A "Particle to Grid Transfer");
+ *   - grid update v = mv/m + dt*g, then walls (App. A "Grid Update");
+ *   - G2P: v_p, C_p = 4/dx^2 sum w v (x_i - x_p)^T, x += dt v (App. A
+ *     "Grid to Particle Transfer"); F <- (I + dt C) F (MLS-MPM form);
+ *   - fixed-corotated Kirchhoff stress (App. B.1, CorotatedElasticity) and
+ *     Neo-Hookean (App. A, eq. neo_hookean, times F^T);
+ *   - Lame parameters from (E, nu) (App. B.1);
+ *   - von Mises and Drucker-Prager return maps on log singular values
+ *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2).
+ * Readings where the paper is silent are listed in the design doc (interpolation
+ * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
+ * delta-gamma of Klar et al. 2016, the 1e-4 floor before log).
+ *
+ * Matrices are 3x3 row-major doubles.  Grids are dense, node (I,J,K) at
+ * ((I*res1)+J)*res2+K, positions I*dx.
+ *
+ * The SVD here is cyclic Jacobi on F^T F; the CUDA path uses a different,
+ * closed-form method.  Results are compared only on invariant quantities.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Configuration and per-particle material description                      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int res[3];          /* grid nodes per axis */
+    double dx, dt;
+    double gravity[3];
+    int bound;           /* wall band thickness in nodes */
+    int wall[6];         /* faces x-, x+, y-, y+, z-, z+ : 0 open, 1 slip, 2 sticky */
+} orc_cfg;
+
+typedef struct {
+    const double *mass;      /* m_p = rho V_p */
+    const double *vol;       /* V_p */
+    const double *logE;      /* log Young's modulus */
+    const double *nu;        /* Poisson ratio */
+    const double *yield;     /* von Mises yield stress sigma_y */
+    const double *phi_deg;   /* Drucker-Prager friction angle, degrees */
+    const int *elastic;      /* 0 fixed-corotated, 1 Neo-Hookean */
+    const int *plastic;      /* 0 identity, 1 von Mises, 2 Drucker-Prager */
+} orc_material;
+
+enum { ORC_OK = 0, ORC_OUT_OF_DOMAIN = 1, ORC_NONFINITE = 2 };
+
+#define SIGMA_FLOOR 1e-4     /* floor on singular values before the log */
+
+/* ------------------------------------------------------------------------ */
+/* Small dense 3x3 helpers                                                   */
+/* ------------------------------------------------------------------------ */
+
+static void m_zero(double A[9]) { memset(A, 0, 9 * sizeof(double)); }
+static void m_eye(double A[9]) { m_zero(A); A[0] = A[4] = A[8] = 1.0; }
+static void m_copy(double D[9], const double A[9]) { memcpy(D, A, 9 * sizeof(double)); }
+
+static void m_mul(double D[9], const double A[9], const double B[9]) {      /* D = A B */
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * k + j];
+            T[3 * i + j] = s;
+        }
+    m_copy(D, T);
+}
+static void m_mul_tn(double D[9], const double A[9], const double B[9]) {   /* D = A^T B */
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * k + i] * B[3 * k + j];
+            T[3 * i + j] = s;
+        }
+    m_copy(D, T);
+}
+static void m_mul_nt(double D[9], const double A[9], const double B[9]) {   /* D = A B^T */
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k) s += A[3 * i + k] * B[3 * j + k];
+            T[3 * i + j] = s;
+        }
+    m_copy(D, T);
+}
+static void m_transpose(double D[9], const double A[9]) {
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = A[3 * j + i];
+    m_copy(D, T);
+}
+static double m_det(const double A[9]) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6])
+         + A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+/* cofactor matrix: cof(A) = det(A) A^{-T} */
+static void m_cofactor(double D[9], const double A[9]) {
+    D[0] = A[4] * A[8] - A[5] * A[7];
+    D[1] = A[5] * A[6] - A[3] * A[8];
+    D[2] = A[3] * A[7] - A[4] * A[6];
+    D[3] = A[2] * A[7] - A[1] * A[8];
+    D[4] = A[0] * A[8] - A[2] * A[6];
+    D[5] = A[1] * A[6] - A[0] * A[7];
+    D[6] = A[1] * A[5] - A[2] * A[4];
+    D[7] = A[2] * A[3] - A[0] * A[5];
+    D[8] = A[0] * A[4] - A[1] * A[3];
+}
+static double m_dot(const double A[9], const double B[9]) {
+    double s = 0.0;
+    for (int i = 0; i < 9; ++i) s += A[i] * B[i];
+    return s;
+}
+static double m_trace(const double A[9]) { return A[0] + A[4] + A[8]; }
+
+static void v_cross(double c[3], const double a[3], const double b[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double v_dot(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* ------------------------------------------------------------------------ */
+/* Quadratic B-spline weights (the interpolation kernel N(x_i - x_p) of the  */
+/* §4.2 momentum equation; the paper names no kernel, the quadratic B-spline  */
+/* is the reading taken).  fx = x/dx - base, base = floor(x/dx - 0.5).        */
+/* ------------------------------------------------------------------------ */
+
+void orc_bspline(double fx, double w[3], double dw[3]) {
+    w[0] = 0.5 * (1.5 - fx) * (1.5 - fx);
+    w[1] = 0.75 - (fx - 1.0) * (fx - 1.0);
+    w[2] = 0.5 * (fx - 0.5) * (fx - 0.5);
+    dw[0] = fx - 1.5;             /* d w / d fx */
+    dw[1] = -2.0 * (fx - 1.0);
+    dw[2] = fx - 0.5;
+}
+
+/* base cell and fractional offset of a particle; returns 0 when the 3x3x3
+ * stencil lies inside the grid, nonzero otherwise. */
+static int locate(const orc_cfg *cfg, const double x[3], int base[3], double fx[3]) {
+    for (int d = 0; d < 3; ++d) {
+        double X = x[d] / cfg->dx;
+        if (!(X == X)) return ORC_NONFINITE;
+        double b = floor(X - 0.5);
+        if (b < 0.0 || b > (double)(cfg->res[d] - 3)) return ORC_OUT_OF_DOMAIN;
+        base[d] = (int)b;
+        fx[d] = X - b;
+    }
+    return ORC_OK;
+}
+
+static long node_index(const orc_cfg *cfg, int I, int J, int K) {
+    return ((long)I * cfg->res[1] + J) * cfg->res[2] + K;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lame parameters from (E, nu), App. B.1                                    */
+/* ------------------------------------------------------------------------ */
+
+void orc_lame(double E, double nu, double *mu, double *lam) {
+    *mu = E / (2.0 * (1.0 + nu));
+    *lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+}
+
+/* d(mu, lambda) / d(log E, nu) */
+static void lame_grad(double logE, double nu, double d[4] /* dmu/dlogE, dmu/dnu, dlam/dlogE, dlam/dnu */) {
+    double E = exp(logE), mu, lam;
+    orc_lame(E, nu, &mu, &lam);
+    double q = (1.0 + nu) * (1.0 - 2.0 * nu);
+    d[0] = mu;
+    d[1] = -E / (2.0 * (1.0 + nu) * (1.0 + nu));
+    d[2] = lam;
+    d[3] = E * (1.0 + 2.0 * nu * nu) / (q * q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3x3 SVD by cyclic Jacobi on F^T F.                                        */
+/* Convention (reading of the paper, which states none): det U = det V = +1,  */
+/* singular values sorted s0 >= s1 >= |s2|, the last one carries sign(det F). */
+/* ------------------------------------------------------------------------ */
+
+static void sym_eig_jacobi(const double Ain[9], double V[9], double lam[3]) {
+    double A[9];
+    m_copy(A, Ain);
+    m_eye(V);
+    static const int P[3] = {0, 0, 1}, Q[3] = {1, 2, 2};
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        double dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off == 0.0 || off <= 1e-40 * dia) break;
+        for (int r = 0; r < 3; ++r) {
+            int p = P[r], q = Q[r];
+            double apq = A[3 * p + q];
+            if (apq == 0.0) continue;
+            double app = A[3 * p + p], aqq = A[3 * q + q];
+            double theta = (aqq - app) / (2.0 * apq);
+            double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            /* A <- J^T A J with J the rotation in the (p,q) plane */
+            for (int k = 0; k < 3; ++k) {       /* columns p, q */
+                double akp = A[3 * k + p], akq = A[3 * k + q];
+                A[3 * k + p] = c * akp - s * akq;
+                A[3 * k + q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {       /* rows p, q */
+                double apk = A[3 * p + k], aqk = A[3 * q + k];
+                A[3 * p + k] = c * apk - s * aqk;
+                A[3 * q + k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {       /* V <- V J */
+                double vkp = V[3 * k + p], vkq = V[3 * k + q];
+                V[3 * k + p] = c * vkp - s * vkq;
+                V[3 * k + q] = s * vkp + c * vkq;
+            }
+        }
+    }
+    lam[0] = A[0]; lam[1] = A[4]; lam[2] = A[8];
+}
+
+static void any_orthogonal_unit(const double a[3], double out[3]) {
+    /* unit vector orthogonal to unit vector a */
+    double e[3] = {0, 0, 0};
+    int k = (fabs(a[0]) <= fabs(a[1]) && fabs(a[0]) <= fabs(a[2])) ? 0 : (fabs(a[1]) <= fabs(a[2]) ? 1 : 2);
+    e[k] = 1.0;
+    double c[3];
+    v_cross(c, a, e);
+    double n = sqrt(v_dot(c, c));
+    out[0] = c[0] / n; out[1] = c[1] / n; out[2] = c[2] / n;
+}
+
+void orc_svd(const double F[9], double U[9], double S[3], double V[9]) {
+    double A[9], lam[3], W[9];
+    m_mul_tn(A, F, F);
+    sym_eig_jacobi(A, W, lam);
+    /* sort eigenpairs descending */
+    int idx[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (lam[idx[j]] > lam[idx[i]]) { int t = idx[i]; idx[i] = idx[j]; idx[j] = t; }
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) V[3 * r + c] = W[3 * r + idx[c]];
+    if (m_det(V) < 0.0)
+        for (int r = 0; r < 3; ++r) V[3 * r + 2] = -V[3 * r + 2];
+    /* U columns from F V with Gram-Schmidt; u2 = u0 x u1 makes det U = +1 */
+    double FV[9];
+    m_mul(FV, F, V);
+    double f0[3] = {FV[0], FV[3], FV[6]}, f1[3] = {FV[1], FV[4], FV[7]}, f2[3] = {FV[2], FV[5], FV[8]};
+    double u0[3], u1[3], u2[3];
+    double n0 = sqrt(v_dot(f0, f0));
+    if (n0 > 0.0) { u0[0] = f0[0] / n0; u0[1] = f0[1] / n0; u0[2] = f0[2] / n0; }
+    else { u0[0] = V[0]; u0[1] = V[3]; u0[2] = V[6]; }
+    double p = v_dot(u0, f1);
+    double r1[3] = {f1[0] - p * u0[0], f1[1] - p * u0[1], f1[2] - p * u0[2]};
+    double n1 = sqrt(v_dot(r1, r1));
+    if (n1 > 1e-300) { u1[0] = r1[0] / n1; u1[1] = r1[1] / n1; u1[2] = r1[2] / n1; }
+    else any_orthogonal_unit(u0, u1);
+    v_cross(u2, u0, u1);
+    for (int r = 0; r < 3; ++r) { U[3 * r + 0] = u0[r]; U[3 * r + 1] = u1[r]; U[3 * r + 2] = u2[r]; }
+    S[0] = v_dot(u0, f0);
+    S[1] = v_dot(u1, f1);
+    S[2] = v_dot(u2, f2);
+}
+
+static void usvt(double D[9], const double U[9], const double s[3], const double V[9]) {
+    double T[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) T[3 * i + j] = U[3 * i + j] * s[j];
+    m_mul_nt(D, T, V);
+}
+
+/* polar rotation R = U V^T of F = R S */
+void orc_polar(const double F[9], double R[9]) {
+    double U[9], S[3], V[9];
+    orc_svd(F, U, S, V);
+    m_mul_nt(R, U, V);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Elasticity: Kirchhoff stress tau = P F^T                                  */
+/*   fixed-corotated: tau = 2 mu (F - R) F^T + lambda J (J - 1) I  (App. B.1)  */
+/*   Neo-Hookean: P = mu (F - F^{-T}) + lambda log J F^{-T} (App. A), so      */
+/*                tau = mu (F F^T - I) + lambda log J I                        */
+/* ------------------------------------------------------------------------ */
+
+int orc_kirchhoff(int model, const double F[9], double mu, double lam, double tau[9]) {
+    double J = m_det(F);
+    if (model == 0) {
+        double R[9], M[9];
+        orc_polar(F, R);
+        for (int i = 0; i < 9; ++i) M[i] = F[i] - R[i];
+        m_mul_nt(tau, M, F);
+        for (int i = 0; i < 9; ++i) tau[i] *= 2.0 * mu;
+        double vol = lam * J * (J - 1.0);
+        tau[0] += vol; tau[4] += vol; tau[8] += vol;
+        return ORC_OK;
+    }
+    if (!(J > 0.0)) return ORC_NONFINITE;       /* log J undefined (reading 13) */
+    m_mul_nt(tau, F, F);
+    tau[0] -= 1.0; tau[4] -= 1.0; tau[8] -= 1.0;
+    for (int i = 0; i < 9; ++i) tau[i] *= mu;
+    double vol = lam * log(J);
+    tau[0] += vol; tau[4] += vol; tau[8] += vol;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Plasticity (App. A eq. von_mises / eq. drucker_prager, App. B.2).          */
+/* psi(F) = U Z(Sigma) V^T with eps = log(max(Sigma, floor)).                 */
+/* Drucker-Prager delta-gamma: the strain-space return map of Klar et al.     */
+/* 2016 (cited by the paper), zero cohesion:                                  */
+/*   alpha = sqrt(2/3) 2 sin(phi) / (3 - sin(phi)),                           */
+/*   dgamma = |eps_hat| + (3 lambda + 2 mu)/(2 mu) tr(eps) alpha.             */
+/* The map is written as z_i = exp(h_i) and reports which case applied.       */
+/* ------------------------------------------------------------------------ */
+
+enum { PM_ELASTIC = 0, PM_PROJECT = 1, PM_TIP = 2 };
+
+double orc_dp_alpha(double phi_deg) {
+    double s = sin(phi_deg * M_PI / 180.0);
+    return sqrt(2.0 / 3.0) * 2.0 * s / (3.0 - s);
+}
+
+/* returns the case; z = new singular values */
+static int return_map_sigma(int model, const double s[3], double mu, double lam, double yield,
+                            double phi_deg, double z[3]) {
+    z[0] = s[0]; z[1] = s[1]; z[2] = s[2];
+    if (model == 0) return PM_ELASTIC;
+    double eps[3], tr = 0.0;
+    for (int i = 0; i < 3; ++i) { eps[i] = log(s[i] > SIGMA_FLOOR ? s[i] : SIGMA_FLOOR); tr += eps[i]; }
+    double e[3], nrm = 0.0;
+    for (int i = 0; i < 3; ++i) { e[i] = eps[i] - tr / 3.0; nrm += e[i] * e[i]; }
+    nrm = sqrt(nrm);
+    double dgamma;
+    if (model == 1) {
+        dgamma = nrm - yield / (2.0 * mu);
+        if (dgamma <= 0.0) return PM_ELASTIC;
+    } else {
+        if (tr > 0.0) { z[0] = z[1] = z[2] = 1.0; return PM_TIP; }
+        double alpha = orc_dp_alpha(phi_deg);
+        dgamma = nrm + (3.0 * lam + 2.0 * mu) / (2.0 * mu) * tr * alpha;
+        if (dgamma <= 0.0) return PM_ELASTIC;
+    }
+    for (int i = 0; i < 3; ++i) z[i] = exp(eps[i] - dgamma * e[i] / nrm);
+    return PM_PROJECT;
+}
+
+int orc_return_map(int model, const double F[9], double mu, double lam, double yield, double phi_deg,
+                   double Fout[9]) {
+    if (model == 0) { m_copy(Fout, F); return PM_ELASTIC; }
+    double U[9], S[3], V[9], z[3];
+    orc_svd(F, U, S, V);
+    int c = return_map_sigma(model, S, mu, lam, yield, phi_deg, z);
+    if (c == PM_ELASTIC) { m_copy(Fout, F); return c; }
+    usvt(Fout, U, z, V);
+    return c;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Forward substep pieces                                                    */
+/* ------------------------------------------------------------------------ */
+
+static void particle_lame(const orc_material *mat, long p, double *mu, double *lam) {
+    orc_lame(exp(mat->logE[p]), mat->nu[p], mu, lam);
+}
+
+/* P2G (§4.2 momentum equation; App. A): grid_m[node], grid_mv[3*node] are
+ * zeroed and accumulated. */
+int orc_p2g(const orc_cfg *cfg, long n, const double *x, const double *v, const double *C, const double *F,
+            const orc_material *mat, double *grid_m, double *grid_mv) {
+    long nn = (long)cfg->res[0] * cfg->res[1] * cfg->res[2];
+    memset(grid_m, 0, nn * sizeof(double));
+    memset(grid_mv, 0, 3 * nn * sizeof(double));
+    double dx = cfg->dx, dt = cfg->dt;
+    for (long p = 0; p < n; ++p) {
+        int base[3]; double fx[3];
+        int st = locate(cfg, x + 3 * p, base, fx);
+        if (st) return st;
+        double mu, lam, tau[9];
+        particle_lame(mat, p, &mu, &lam);
+        st = orc_kirchhoff(mat->elastic[p], F + 9 * p, mu, lam, tau);
+        if (st) return st;
+        double mp = mat->mass[p], Vp = mat->vol[p];
+        double k = 4.0 * dt * Vp / (dx * dx);
+        double A[9];
+        for (int i = 0; i < 9; ++i) A[i] = mp * C[9 * p + i] - k * tau[i];
+        double w[3][3], dw[3][3];
+        for (int d = 0; d < 3; ++d) orc_bspline(fx[d], w[d], dw[d]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                    double wt = w[0][i] * w[1][j] * w[2][l];
+                    double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (l - fx[2]) * dx};
+                    long nd = node_index(cfg, base[0] + i, base[1] + j, base[2] + l);
+                    grid_m[nd] += wt * mp;
+                    for (int r = 0; r < 3; ++r) {
+                        double Ad = A[3 * r] * dpos[0] + A[3 * r + 1] * dpos[1] + A[3 * r + 2] * dpos[2];
+                        grid_mv[3 * nd + r] += wt * (mp * v[3 * p + r] + Ad);
+                    }
+                }
+    }
+    return ORC_OK;
+}
+
+/* Wall rule (reading; the paper states none): band of cfg->bound nodes on each
+ * face.  A sticky face zeroes the whole velocity; a slip face zeroes the
+ * normal component when it points out of the domain.  Returns per-component
+ * pass-through mask (1 keeps the component, 0 zeroes it). */
+static void wall_mask(const orc_cfg *cfg, const int I[3], const double u[3], double mask[3]) {
+    mask[0] = mask[1] = mask[2] = 1.0;
+    int sticky = 0;
+    for (int d = 0; d < 3; ++d) {
+        if (I[d] < cfg->bound && cfg->wall[2 * d] == 2) sticky = 1;
+        if (I[d] >= cfg->res[d] - cfg->bound && cfg->wall[2 * d + 1] == 2) sticky = 1;
+    }
+    if (sticky) { mask[0] = mask[1] = mask[2] = 0.0; return; }
+    for (int d = 0; d < 3; ++d) {
+        if (I[d] < cfg->bound && cfg->wall[2 * d] == 1 && u[d] < 0.0) mask[d] = 0.0;
+        if (I[d] >= cfg->res[d] - cfg->bound && cfg->wall[2 * d + 1] == 1 && u[d] > 0.0) mask[d] = 0.0;
+    }
+}
+
+/* Grid update (App. A): v = mv/m + dt g for m > 0, then walls; v = 0 where m = 0. */
+void orc_grid_update(const orc_cfg *cfg, const double *grid_m, const double *grid_mv, double *grid_v) {
+    for (int I = 0; I < cfg->res[0]; ++I)
+        for (int J = 0; J < cfg->res[1]; ++J)
+            for (int K = 0; K < cfg->res[2]; ++K) {
+                long nd = node_index(cfg, I, J, K);
+                double *vv = grid_v + 3 * nd;
+                if (!(grid_m[nd] > 0.0)) { vv[0] = vv[1] = vv[2] = 0.0; continue; }
+                double u[3], mask[3];
+                for (int d = 0; d < 3; ++d) u[d] = grid_mv[3 * nd + d] / grid_m[nd] + cfg->dt * cfg->gravity[d];
+                int idx[3] = {I, J, K};
+                wall_mask(cfg, idx, u, mask);
+                for (int d = 0; d < 3; ++d) vv[d] = mask[d] * u[d];
+            }
+}
+
+/* G2P + advection + F update + plasticity (App. A; Algorithm 1 Stage 1).
+ * Reads x, F (old); writes x, v, C, F (new) in place. */
+int orc_g2p(const orc_cfg *cfg, long n, double *x, double *v, double *C, double *F,
+            const orc_material *mat, const double *grid_v) {
+    double dx = cfg->dx, dt = cfg->dt;
+    for (long p = 0; p < n; ++p) {
+        int base[3]; double fx[3];
+        int st = locate(cfg, x + 3 * p, base, fx);
+        if (st) return st;
+        double w[3][3], dw[3][3];
+        for (int d = 0; d < 3; ++d) orc_bspline(fx[d], w[d], dw[d]);
+        double vp[3] = {0, 0, 0}, Bp[9];
+        m_zero(Bp);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                    double wt = w[0][i] * w[1][j] * w[2][l];
+                    double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (l - fx[2]) * dx};
+                    const double *vi = grid_v + 3 * node_index(cfg, base[0] + i, base[1] + j, base[2] + l);
+                    for (int r = 0; r < 3; ++r) {
+                        vp[r] += wt * vi[r];
+                        for (int c = 0; c < 3; ++c) Bp[3 * r + c] += wt * vi[r] * dpos[c];
+                    }
+                }
+        double Cn[9], G[9], Fn[9];
+        for (int i = 0; i < 9; ++i) Cn[i] = 4.0 / (dx * dx) * Bp[i];
+        double IC[9];
+        for (int i = 0; i < 9; ++i) IC[i] = dt * Cn[i];
+        IC[0] += 1.0; IC[4] += 1.0; IC[8] += 1.0;
+        m_mul(G, IC, F + 9 * p);
+        double mu, lam;
+        particle_lame(mat, p, &mu, &lam);
+        orc_return_map(mat->plastic[p], G, mu, lam, mat->yield[p], mat->phi_deg[p], Fn);
+        for (int r = 0; r < 3; ++r) { v[3 * p + r] = vp[r]; x[3 * p + r] += dt * vp[r]; }
+        m_copy(C + 9 * p, Cn);
+        m_copy(F + 9 * p, Fn);
+    }
+    return ORC_OK;
+}
+
+static long n_nodes(const orc_cfg *cfg) { return (long)cfg->res[0] * cfg->res[1] * cfg->res[2]; }
+
+/* one full substep in place */
+int orc_substep(const orc_cfg *cfg, long n, double *x, double *v, double *C, double *F, const orc_material *mat) {
+    long nn = n_nodes(cfg);
+    double *gm = (double *)malloc(nn * sizeof(double));
+    double *gmv = (double *)malloc(3 * nn * sizeof(double));
+    double *gv = (double *)malloc(3 * nn * sizeof(double));
+    int st = orc_p2g(cfg, n, x, v, C, F, mat, gm, gmv);
+    if (!st) {
+        orc_grid_update(cfg, gm, gmv, gv);
+        st = orc_g2p(cfg, n, x, v, C, F, mat, gv);
+    }
+    free(gm); free(gmv); free(gv);
+    return st;
+}
+
+/* Runs n_sub substeps.  When tape != NULL it receives (n_sub+1) snapshots of
+ * the state, each n x 24 doubles laid out [x(3) v(3) C(9) F(9)] per particle. */
+static void pack_state(double *dst, long n, const double *x, const double *v, const double *C, const double *F) {
+    for (long p = 0; p < n; ++p) {
+        double *r = dst + 24 * p;
+        memcpy(r, x + 3 * p, 3 * sizeof(double));
+        memcpy(r + 3, v + 3 * p, 3 * sizeof(double));
+        memcpy(r + 6, C + 9 * p, 9 * sizeof(double));
+        memcpy(r + 15, F + 9 * p, 9 * sizeof(double));
+    }
+}
+static void unpack_state(const double *src, long n, double *x, double *v, double *C, double *F) {
+    for (long p = 0; p < n; ++p) {
+        const double *r = src + 24 * p;
+        memcpy(x + 3 * p, r, 3 * sizeof(double));
+        memcpy(v + 3 * p, r + 3, 3 * sizeof(double));
+        memcpy(C + 9 * p, r + 6, 9 * sizeof(double));
+        memcpy(F + 9 * p, r + 15, 9 * sizeof(double));
+    }
+}
+
+int orc_run(const orc_cfg *cfg, long n, double *x, double *v, double *C, double *F, const orc_material *mat,
+            int n_sub, double *tape) {
+    if (tape) pack_state(tape, n, x, v, C, F);
+    for (int s = 0; s < n_sub; ++s) {
+        int st = orc_substep(cfg, n, x, v, C, F, mat);
+        if (st) return st;
+        if (tape) pack_state(tape + (long)(s + 1) * n * 24, n, x, v, C, F);
+    }
+    return ORC_OK;
+}
+
+/* ======================================================================== */
+/* Adjoint (reverse mode) of one substep, derived by hand from the forward   */
+/* above.  Given the state at the start of the substep and the adjoint of     */
+/* the state at its end, it returns the adjoint of the start state and adds   */
+/* the parameter gradients (d/d logE, d/d nu, d/d yield) into g_param.        */
+/* ======================================================================== */
+
+/* adjoint of the polar rotation R = U V^T:  Fbar += U Y V^T with
+ * K = U^T Rbar V, Y_ij = (K_ij - K_ji) / (s_i + s_j), Y_ii = 0. */
+static void polar_adjoint(const double U[9], const double S[3], const double V[9], const double Rbar[9],
+                          double Fbar[9]) {
+    double K[9], T[9], Y[9];
+    m_mul_tn(T, U, Rbar);
+    m_mul(K, T, V);
+    m_zero(Y);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (i != j) Y[3 * i + j] = (K[3 * i + j] - K[3 * j + i]) / (S[i] + S[j]);
+    double D[9];
+    m_mul(T, U, Y);
+    m_mul_nt(D, T, V);
+    for (int i = 0; i < 9; ++i) Fbar[i] += D[i];
+}
+
+/* adjoint of the Kirchhoff stress; adds to Fbar, mubar, lambar */
+static void kirchhoff_adjoint(int model, const double F[9], double mu, double lam, const double taubar[9],
+                              double Fbar[9], double *mubar, double *lambar) {
+    double J = m_det(F), cof[9];
+    m_cofactor(cof, F);                  /* dJ/dF */
+    double trb = m_trace(taubar);
+    if (model == 0) {
+        double U[9], S[3], V[9], R[9], M[9], T[9];
+        orc_svd(F, U, S, V);
+        m_mul_nt(R, U, V);
+        for (int i = 0; i < 9; ++i) M[i] = F[i] - R[i];
+        /* tau = 2 mu M F^T + lam J (J-1) I */
+        m_mul_nt(T, M, F);
+        *mubar += 2.0 * m_dot(taubar, T);
+        *lambar += trb * J * (J - 1.0);
+        double Mbar[9], TbF[9];
+        m_mul(Mbar, taubar, F);                 /* d/dM of <taubar, M F^T> */
+        for (int i = 0; i < 9; ++i) Mbar[i] *= 2.0 * mu;
+        m_mul_tn(TbF, taubar, M);               /* d/dF of <taubar, M F^T> via F^T: taubar^T M */
+        for (int i = 0; i < 9; ++i) Fbar[i] += Mbar[i] + 2.0 * mu * TbF[i];
+        double Rbar[9];
+        for (int i = 0; i < 9; ++i) Rbar[i] = -Mbar[i];
+        polar_adjoint(U, S, V, Rbar, Fbar);
+        double Jbar = lam * trb * (2.0 * J - 1.0);
+        for (int i = 0; i < 9; ++i) Fbar[i] += Jbar * cof[i];
+    } else {
+        /* tau = mu (F F^T - I) + lam log J I */
+        double FFt[9], T[9];
+        m_mul_nt(FFt, F, F);
+        FFt[0] -= 1.0; FFt[4] -= 1.0; FFt[8] -= 1.0;
+        *mubar += m_dot(taubar, FFt);
+        *lambar += trb * log(J);
+        double S2[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S2[3 * i + j] = taubar[3 * i + j] + taubar[3 * j + i];
+        m_mul(T, S2, F);
+        for (int i = 0; i < 9; ++i) Fbar[i] += mu * T[i] + lam * trb / J * cof[i];
+    }
+}
+
+/* z(sigma) of the return map and its derivatives:
+ *   Jz[i][k] = d z_i / d sigma_k, dz_dmu[i], dz_dlam[i], dz_dy[i]. */
+static int return_map_jacobian(int model, const double s[3], double mu, double lam, double yield, double phi_deg,
+                               double z[3], double Jz[9], double dz_dmu[3], double dz_dlam[3], double dz_dy[3]) {
+    int c = return_map_sigma(model, s, mu, lam, yield, phi_deg, z);
+    for (int i = 0; i < 3; ++i) { dz_dmu[i] = dz_dlam[i] = dz_dy[i] = 0.0; }
+    m_zero(Jz);
+    if (c == PM_ELASTIC) { Jz[0] = Jz[4] = Jz[8] = 1.0; return c; }
+    if (c == PM_TIP) return c;
+    double eps[3], tr = 0.0, deps[3];
+    for (int i = 0; i < 3; ++i) {
+        int clamped = !(s[i] > SIGMA_FLOOR);
+        eps[i] = log(clamped ? SIGMA_FLOOR : s[i]);
+        deps[i] = clamped ? 0.0 : 1.0 / s[i];
+        tr += eps[i];
+    }
+    double e[3], nrm = 0.0;
+    for (int i = 0; i < 3; ++i) { e[i] = eps[i] - tr / 3.0; nrm += e[i] * e[i]; }
+    nrm = sqrt(nrm);
+    double dgamma, ddg_deps[3], ddg_dmu, ddg_dlam, ddg_dy;
+    if (model == 1) {
+        dgamma = nrm - yield / (2.0 * mu);
+        for (int k = 0; k < 3; ++k) ddg_deps[k] = e[k] / nrm;
+        ddg_dmu = yield / (2.0 * mu * mu);
+        ddg_dlam = 0.0;
+        ddg_dy = -1.0 / (2.0 * mu);
+    } else {
+        double alpha = orc_dp_alpha(phi_deg);
+        double kap = (3.0 * lam + 2.0 * mu) / (2.0 * mu) * alpha;
+        dgamma = nrm + kap * tr;
+        for (int k = 0; k < 3; ++k) ddg_deps[k] = e[k] / nrm + kap;
+        ddg_dmu = tr * (-3.0 * lam * alpha / (2.0 * mu * mu));
+        ddg_dlam = tr * (3.0 * alpha / (2.0 * mu));
+        ddg_dy = 0.0;
+    }
+    /* h_i = eps_i - dgamma e_i / nrm ; z_i = exp(h_i) */
+    for (int i = 0; i < 3; ++i) {
+        for (int k = 0; k < 3; ++k) {
+            double Pik = (i == k ? 1.0 : 0.0) - 1.0 / 3.0;
+            double dunit = (Pik - e[i] * e[k] / (nrm * nrm)) / nrm;   /* d(e_i/nrm)/d eps_k */
+            double dh = (i == k ? 1.0 : 0.0) - ddg_deps[k] * e[i] / nrm - dgamma * dunit;
+            Jz[3 * i + k] = z[i] * dh * deps[k];
+        }
+        dz_dmu[i] = -z[i] * ddg_dmu * e[i] / nrm;
+        dz_dlam[i] = -z[i] * ddg_dlam * e[i] / nrm;
+        dz_dy[i] = -z[i] * ddg_dy * e[i] / nrm;
+    }
+    return c;
+}
+
+/* adjoint of psi(G) = U diag(z(sigma)) V^T.  K = U^T Fbar_out V;
+ *   sigma_bar_k = sum_i K_ii dz_i/dsigma_k;
+ *   off-diagonal: Y_ij = K_ij (A+B)/2 + K_ji (A-B)/2, with
+ *   A = (z_i - z_j)/(s_i - s_j) (divided difference; at s_i = s_j its limit
+ *   dz_i/ds_i - dz_i/ds_j for an isotropic map) and B = (z_i + z_j)/(s_i + s_j). */
+static void plastic_adjoint(int model, const double G[9], double mu, double lam, double yield, double phi_deg,
+                            const double Fbar_out[9], double Gbar[9], double *mubar, double *lambar, double *ybar) {
+    if (model == 0) { m_copy(Gbar, Fbar_out); return; }
+    double U[9], S[3], V[9], z[3], Jz[9], dmu[3], dlam[3], dy[3];
+    orc_svd(G, U, S, V);
+    int c = return_map_jacobian(model, S, mu, lam, yield, phi_deg, z, Jz, dmu, dlam, dy);
+    if (c == PM_ELASTIC) { m_copy(Gbar, Fbar_out); return; }
+    double K[9], T[9], Y[9];
+    m_mul_tn(T, U, Fbar_out);
+    m_mul(K, T, V);
+    m_zero(Y);
+    for (int k = 0; k < 3; ++k) {
+        double sb = 0.0;
+        for (int i = 0; i < 3; ++i) sb += K[4 * i] * Jz[3 * i + k];
+        Y[4 * k] = sb;
+    }
+    for (int i = 0; i < 3; ++i) {
+        *mubar += K[4 * i] * dmu[i];
+        *lambar += K[4 * i] * dlam[i];
+        *ybar += K[4 * i] * dy[i];
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) continue;
+            double A, B;
+            double ds = S[i] - S[j], scale = fabs(S[i]) + fabs(S[j]);
+            if (fabs(ds) > 1e-6 * scale) A = (z[i] - z[j]) / ds;
+            else A = Jz[3 * i + i] - Jz[3 * i + j];
+            B = (z[i] + z[j]) / (S[i] + S[j]);
+            Y[3 * i + j] = K[3 * i + j] * 0.5 * (A + B) + K[3 * j + i] * 0.5 * (A - B);
+        }
+    m_mul(T, U, Y);
+    m_mul_nt(Gbar, T, V);
+}
+
+/* adj layout per particle: [x(3) v(3) C(9) F(9)].  adj_out is the adjoint of
+ * the end state; adj_in receives the adjoint of the start state.  g_param is
+ * n x 3 (logE, nu, yield), accumulated. */
+int orc_substep_adjoint(const orc_cfg *cfg, long n, const double *state, const orc_material *mat,
+                        const double *adj_out, double *adj_in, double *g_param) {
+    long nn = n_nodes(cfg);
+    double dx = cfg->dx, dt = cfg->dt, inv_dx2 = 1.0 / (dx * dx);
+    double *x = (double *)malloc(3 * n * sizeof(double)), *v = (double *)malloc(3 * n * sizeof(double));
+    double *C = (double *)malloc(9 * n * sizeof(double)), *F = (double *)malloc(9 * n * sizeof(double));
+    unpack_state(state, n, x, v, C, F);
+    double *gm = (double *)calloc(nn, sizeof(double)), *gP = (double *)calloc(3 * nn, sizeof(double));
+    double *gv = (double *)calloc(3 * nn, sizeof(double)), *gmask = (double *)calloc(3 * nn, sizeof(double));
+    double *gvbar = (double *)calloc(3 * nn, sizeof(double));
+    double *gmbar = (double *)calloc(nn, sizeof(double)), *gPbar = (double *)calloc(3 * nn, sizeof(double));
+    int st = orc_p2g(cfg, n, x, v, C, F, mat, gm, gP);
+    if (st) goto done;
+    /* grid update, keeping the wall masks */
+    for (int I = 0; I < cfg->res[0]; ++I)
+        for (int J = 0; J < cfg->res[1]; ++J)
+            for (int K = 0; K < cfg->res[2]; ++K) {
+                long nd = node_index(cfg, I, J, K);
+                if (!(gm[nd] > 0.0)) continue;
+                double u[3], mask[3];
+                for (int d = 0; d < 3; ++d) u[d] = gP[3 * nd + d] / gm[nd] + dt * cfg->gravity[d];
+                int idx[3] = {I, J, K};
+                wall_mask(cfg, idx, u, mask);
+                for (int d = 0; d < 3; ++d) { gv[3 * nd + d] = mask[d] * u[d]; gmask[3 * nd + d] = mask[d]; }
+            }
+    /* G2P reverse: scatter onto grid velocity adjoints, partial particle adjoints */
+    for (long p = 0; p < n; ++p) {
+        const double *ao = adj_out + 24 * p;
+        double *ai = adj_in + 24 * p;
+        memset(ai, 0, 24 * sizeof(double));
+        int base[3]; double fx[3];
+        locate(cfg, x + 3 * p, base, fx);
+        double w[3][3], dw[3][3];
+        for (int d = 0; d < 3; ++d) orc_bspline(fx[d], w[d], dw[d]);
+        /* recompute v', C' */
+        double vp[3] = {0, 0, 0}, Cn[9];
+        m_zero(Cn);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                    double wt = w[0][i] * w[1][j] * w[2][l];
+                    double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (l - fx[2]) * dx};
+                    const double *vi = gv + 3 * node_index(cfg, base[0] + i, base[1] + j, base[2] + l);
+                    for (int r = 0; r < 3; ++r) {
+                        vp[r] += wt * vi[r];
+                        for (int c = 0; c < 3; ++c) Cn[3 * r + c] += 4.0 * inv_dx2 * wt * vi[r] * dpos[c];
+                    }
+                }
+        double IC[9], G[9];
+        for (int i = 0; i < 9; ++i) IC[i] = dt * Cn[i];
+        IC[0] += 1.0; IC[4] += 1.0; IC[8] += 1.0;
+        m_mul(G, IC, F + 9 * p);
+        double mu, lam, mubar = 0.0, lambar = 0.0, ybar = 0.0, Gbar[9];
+        particle_lame(mat, p, &mu, &lam);
+        plastic_adjoint(mat->plastic[p], G, mu, lam, mat->yield[p], mat->phi_deg[p], ao + 15, Gbar,
+                        &mubar, &lambar, &ybar);
+        /* G = (I + dt C') F */
+        double Cbar[9], T[9];
+        m_mul_nt(T, Gbar, F + 9 * p);
+        for (int i = 0; i < 9; ++i) Cbar[i] = ao[6 + i] + dt * T[i];
+        m_mul_tn(T, IC, Gbar);
+        for (int i = 0; i < 9; ++i) ai[15 + i] += T[i];
+        /* x' = x + dt v' */
+        double vbar[3];
+        for (int r = 0; r < 3; ++r) { ai[r] += ao[r]; vbar[r] = ao[3 + r] + dt * ao[r]; }
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                    int o[3] = {i, j, l};
+                    double wt = w[0][i] * w[1][j] * w[2][l];
+                    double gw[3] = {dw[0][i] * w[1][j] * w[2][l] / dx, w[0][i] * dw[1][j] * w[2][l] / dx,
+                                    w[0][i] * w[1][j] * dw[2][l] / dx};
+                    double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (l - fx[2]) * dx};
+                    long nd = node_index(cfg, base[0] + o[0], base[1] + o[1], base[2] + o[2]);
+                    const double *vi = gv + 3 * nd;
+                    double wbar = 0.0, dposbar[3] = {0, 0, 0};
+                    for (int r = 0; r < 3; ++r) {
+                        double cd = Cbar[3 * r] * dpos[0] + Cbar[3 * r + 1] * dpos[1] + Cbar[3 * r + 2] * dpos[2];
+                        gvbar[3 * nd + r] += wt * vbar[r] + 4.0 * inv_dx2 * wt * cd;
+                        wbar += vbar[r] * vi[r] + 4.0 * inv_dx2 * vi[r] * cd;
+                    }
+                    for (int c = 0; c < 3; ++c) {
+                        double s = 0.0;
+                        for (int r = 0; r < 3; ++r) s += Cbar[3 * r + c] * vi[r];
+                        dposbar[c] = 4.0 * inv_dx2 * wt * s;
+                    }
+                    for (int d = 0; d < 3; ++d) ai[d] += wbar * gw[d] - dposbar[d];
+                }
+        double dl[4];
+        lame_grad(mat->logE[p], mat->nu[p], dl);
+        g_param[3 * p + 0] += mubar * dl[0] + lambar * dl[2];
+        g_param[3 * p + 1] += mubar * dl[1] + lambar * dl[3];
+        g_param[3 * p + 2] += ybar;
+    }
+    /* grid update reverse */
+    for (long nd = 0; nd < nn; ++nd) {
+        if (!(gm[nd] > 0.0)) continue;
+        double m = gm[nd], s = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            double ub = gmask[3 * nd + d] * gvbar[3 * nd + d];
+            gPbar[3 * nd + d] = ub / m;
+            s += ub * gP[3 * nd + d];
+        }
+        gmbar[nd] = -s / (m * m);
+    }
+    /* P2G reverse: gather grid adjoints */
+    for (long p = 0; p < n; ++p) {
+        double *ai = adj_in + 24 * p;
+        int base[3]; double fx[3];
+        locate(cfg, x + 3 * p, base, fx);
+        double w[3][3], dw[3][3];
+        for (int d = 0; d < 3; ++d) orc_bspline(fx[d], w[d], dw[d]);
+        double mu, lam, tau[9];
+        particle_lame(mat, p, &mu, &lam);
+        orc_kirchhoff(mat->elastic[p], F + 9 * p, mu, lam, tau);
+        double mp = mat->mass[p], kf = 4.0 * dt * mat->vol[p] * inv_dx2;
+        double A[9], Abar[9];
+        for (int i = 0; i < 9; ++i) A[i] = mp * C[9 * p + i] - kf * tau[i];
+        m_zero(Abar);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                for (int l = 0; l < 3; ++l) {
+                    double wt = w[0][i] * w[1][j] * w[2][l];
+                    double gw[3] = {dw[0][i] * w[1][j] * w[2][l] / dx, w[0][i] * dw[1][j] * w[2][l] / dx,
+                                    w[0][i] * w[1][j] * dw[2][l] / dx};
+                    double dpos[3] = {(i - fx[0]) * dx, (j - fx[1]) * dx, (l - fx[2]) * dx};
+                    long nd = node_index(cfg, base[0] + i, base[1] + j, base[2] + l);
+                    const double *Pb = gPbar + 3 * nd;
+                    double wbar = gmbar[nd] * mp;
+                    double dposbar[3] = {0, 0, 0};
+                    for (int r = 0; r < 3; ++r) {
+                        double Ad = A[3 * r] * dpos[0] + A[3 * r + 1] * dpos[1] + A[3 * r + 2] * dpos[2];
+                        wbar += Pb[r] * (mp * v[3 * p + r] + Ad);
+                        ai[3 + r] += wt * mp * Pb[r];
+                        for (int c = 0; c < 3; ++c) {
+                            Abar[3 * r + c] += wt * Pb[r] * dpos[c];
+                            dposbar[c] += wt * A[3 * r + c] * Pb[r];
+                        }
+                    }
+                    for (int d = 0; d < 3; ++d) ai[d] += wbar * gw[d] - dposbar[d];
+                }
+        double taubar[9], mubar = 0.0, lambar = 0.0;
+        for (int i = 0; i < 9; ++i) { ai[6 + i] += mp * Abar[i]; taubar[i] = -kf * Abar[i]; }
+        kirchhoff_adjoint(mat->elastic[p], F + 9 * p, mu, lam, taubar, ai + 15, &mubar, &lambar);
+        double dl[4];
+        lame_grad(mat->logE[p], mat->nu[p], dl);
+        g_param[3 * p + 0] += mubar * dl[0] + lambar * dl[2];
+        g_param[3 * p + 1] += mubar * dl[1] + lambar * dl[3];
+    }
+done:
+    free(x); free(v); free(C); free(F);
+    free(gm); free(gP); free(gv); free(gmask); free(gvbar); free(gmbar); free(gPbar);
+    return st;
+}
+
+/* Trajectory adjoint.  tape holds (n_sub+1) states from orc_run.  Frame f is
+ * the state after frame_sub[f] substeps; dLdx[f] (n x 3) is the loss gradient
+ * with respect to the positions of that frame.  Writes the adjoint of the
+ * initial state (n x 24) and the parameter gradients (n x 3, overwritten). */
+int orc_backward(const orc_cfg *cfg, long n, const orc_material *mat, int n_sub, const double *tape,
+                 int n_frames, const int *frame_sub, const double *dLdx, double *adj0, double *g_param) {
+    double *a = (double *)calloc(24 * n, sizeof(double)), *b = (double *)calloc(24 * n, sizeof(double));
+    memset(g_param, 0, 3 * n * sizeof(double));
+    int st = ORC_OK;
+    for (int s = n_sub; s >= 0; --s) {
+        for (int f = 0; f < n_frames; ++f)
+            if (frame_sub[f] == s)
+                for (long p = 0; p < n; ++p)
+                    for (int d = 0; d < 3; ++d) a[24 * p + d] += dLdx[((long)f * n + p) * 3 + d];
+        if (s == 0) break;
+        st = orc_substep_adjoint(cfg, n, tape + (long)(s - 1) * n * 24, mat, a, b, g_param);
+        if (st) break;
+        double *t = a; a = b; b = t;
+    }
+    memcpy(adj0, a, 24 * n * sizeof(double));
+    free(a); free(b);
+    return st;
+}
