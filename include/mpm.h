@@ -1,0 +1,170 @@
+/*
+ * mpm.h -- C ABI of libmpm: the MLS-MPM substep (APIC transfers, quadratic
+ * B-spline) of FastPhysGS (arXiv 2602.01723), its adjoint, and its batched
+ * form, on one GPU (sm_103a).
+ *
+ * The method (what every entry point computes) is the substep of the paper's
+ * Algorithm 1, Stage 1:
+ *     tau <- Elasticity(F, E);  (x, v, C, F) <- MPMStep(x, v, C, F, tau);
+ *     F <- Plasticity(F, E)
+ * with MPMStep = P2G (the momentum-exchange equation of §4.2 with the MLS
+ * stress term; App. A "Particle to Grid Transfer"), the grid update (App. A
+ * "Grid Update": v = mv/m + dt g, then walls), and G2P (App. A "Grid to
+ * Particle Transfer", with F <- (I + dt C) F).  Elasticity is fixed-corotated
+ * (App. B.1) or Neo-Hookean (App. A, eq. neo_hookean); plasticity is none,
+ * von Mises (App. A, eq. von_mises) or Drucker-Prager (App. A, eq.
+ * drucker_prager); Lame parameters follow App. B.1.
+ *
+ * Conventions
+ *  - Positions are in world units; grid node (I,J,K) sits at (I,J,K)*dx.  A
+ *    particle must keep its 3x3x3 stencil on the grid: 0.5 dx <= x_d <
+ *    (grid_res_d - 1.5) dx, otherwise MPM_ERR_OUT_OF_DOMAIN is raised.
+ *  - Arrays are contiguous, row-major float32 / int32: x, v are n x 3; C, F
+ *    are n x 9 (3x3 row-major).  Array pointers may be device pointers or
+ *    host pointers (pinned or pageable): the library copies with
+ *    cudaMemcpyDefault on the given stream.  The caller owns every array it
+ *    passes; the library never keeps a caller pointer after a call returns.
+ *  - Particle order is the caller's order in every input and output.
+ *  - stream: a cudaStream_t, or NULL for the legacy default stream.  Calls
+ *    enqueue work on it; they do not synchronise unless stated.
+ *
+ * Errors
+ *  - Every entry point returns mpm_status; no C++ exception crosses the ABI.
+ *  - Argument checks are synchronous.  Conditions found on the device
+ *    (particle leaving the domain, non-finite state, J <= 0 under
+ *    Neo-Hookean, grid pool exhausted, a particle moving more than one cell in
+ *    a substep) set a sticky device error word; mpm_sync and every call that
+ *    synchronises report it, after which the context stays in MPM_ERR_STATE
+ *    until mpm_load_particles succeeds.
+ *  - mpm_last_error gives a human-readable message for the last failure.
+ */
+#ifndef MPM_H
+#define MPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MPM_API __attribute__((visibility("default")))
+#else
+#define MPM_API
+#endif
+
+typedef struct mpm_ctx mpm_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    MPM_OK = 0,
+    MPM_ERR_INVALID_ARG = 1,
+    MPM_ERR_OOM = 2,
+    MPM_ERR_CUDA = 3,
+    MPM_ERR_OUT_OF_DOMAIN = 4,
+    MPM_ERR_NONFINITE = 5,
+    MPM_ERR_TIMEOUT = 6,
+    MPM_ERR_STATE = 7,
+    MPM_ERR_CAPACITY = 8,   /* grid block pool or checkpoint budget exhausted */
+    MPM_ERR_CFL = 9         /* a particle moved more than one grid cell in one substep */
+} mpm_status;
+
+enum { MPM_ELASTIC_FIXED_COROTATED = 0, MPM_ELASTIC_NEO_HOOKEAN = 1 };
+enum { MPM_PLASTIC_NONE = 0, MPM_PLASTIC_VON_MISES = 1, MPM_PLASTIC_DRUCKER_PRAGER = 2 };
+enum { MPM_WALL_OPEN = 0, MPM_WALL_SLIP = 1, MPM_WALL_STICKY = 2 };
+
+/* One entry of the material table (§4.2: each object instance l_k carries
+ * {rho, nu, Phi, E}).  E, nu give the Lame parameters (App. B.1);
+ * yield_stress is the von Mises sigma_y; friction_angle_deg the
+ * Drucker-Prager friction angle (alpha = sqrt(2/3) 2 sin phi / (3 - sin phi),
+ * zero cohesion). */
+typedef struct {
+    int32_t elastic;            /* MPM_ELASTIC_* */
+    int32_t plastic;            /* MPM_PLASTIC_* */
+    float E, nu, rho, yield_stress, friction_angle_deg;
+} mpm_material;
+
+/* Options.  Fill with mpm_default_options, then override. */
+typedef struct {
+    int32_t n_instances;        /* independent problems, each on its own grid of grid_res (default 1) */
+    int32_t bound;              /* wall band thickness in nodes (default 3) */
+    int32_t walls[6];           /* faces x-, x+, y-, y+, z-, z+ (default: y- sticky, others slip) */
+    int64_t max_particles;      /* particle capacity (default 0: set by the first load) */
+    int64_t max_active_blocks;  /* capacity of the 4x4x4-node block pool per grid buffer (0: automatic) */
+    int32_t ckpt_every;         /* checkpoint interval k of the recorded forward pass (default 20) */
+    int32_t chunk;              /* particles per work item of the substep kernel, <= 256 (0: 128) */
+    int32_t threads;            /* unused (the substep kernel runs 128-thread CTAs) */
+    int32_t scatter;            /* P2G scatter: 0 shared-memory float atomics, 1 int32 fixed-point
+                                   shared-memory atomics (default), 2 direct global reductions */
+    int32_t reserved[7];
+} mpm_options;
+
+MPM_API mpm_status mpm_default_options(mpm_options *opt);
+
+/* Creates a context on the current CUDA device.  grid_res: nodes per axis,
+ * each a multiple of 4 and >= 8.  dx > 0, dt > 0.  gravity: 3 floats (host).
+ * table: n_materials >= 1 entries (host), copied.  opt may be NULL. */
+MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, const float gravity[3],
+                              const mpm_material *table, int32_t n_materials, const mpm_options *opt,
+                              mpm_ctx **out);
+
+/* Replaces the particle set.  x, vol, material_id are required; v (NULL: 0),
+ * C (NULL: 0), F (NULL: I) optional; instance (n int32, NULL: all 0) selects
+ * the grid of each particle; params (n x 3 float: log E, nu, yield stress;
+ * NULL: from the material table) overrides the table per particle.  Particle
+ * mass is rho * vol.  Also clears the recorded trajectory.  Synchronises the
+ * stream and reports out-of-range inputs. */
+MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, const float *v, const float *C,
+                                      const float *F, const float *vol, const int32_t *material_id,
+                                      const int32_t *instance, const float *params, void *stream);
+
+/* Advances n_substeps >= 0 substeps.  With record != 0 the state at every
+ * ckpt_every-th substep counted from the last load (or mpm_record_reset) is
+ * kept for mpm_backward; the recording must be contiguous (record on every
+ * call since the last reset).  Does not synchronise. */
+MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, void *stream);
+
+/* Copies the current state out, in the caller's particle order; any pointer
+ * may be NULL.  Enqueued on the stream; does not synchronise. */
+MPM_API mpm_status mpm_get_particles(mpm_ctx *ctx, float *x, float *v, float *C, float *F, void *stream);
+
+/* Reverse pass over the recorded substeps [0, S), S = substeps recorded.
+ * frame_substep (host, n_frames ints in 1..S, any order) names the substep
+ * after which frame f's positions were taken; dL_dx (n_frames x n x 3) is the
+ * loss gradient with respect to those positions.  Writes dL_dparams (n x 3:
+ * d/d log E, d/d nu, d/d yield stress, per particle; required) and, when not
+ * NULL, dL_dstate0 (n x 24: the adjoint of the initial [x v C F]).  Recomputes
+ * each checkpoint segment forward; the recorded state is left unchanged.
+ * Synchronises the stream. */
+MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const int32_t *frame_substep, const float *dL_dx,
+                                float *dL_dparams, float *dL_dstate0, void *stream);
+
+/* Drops the recorded trajectory; the next recorded substep is index 0. */
+MPM_API mpm_status mpm_record_reset(mpm_ctx *ctx);
+
+/* Waits for the context's work on the stream and reports the sticky device
+ * error word. */
+MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream);
+
+/* Diagnostics copied to host (synchronises): counters[0] particles,
+ * [1] occupied blocks, [2] active blocks of the last grid, [3] work chunks,
+ * [4] FP64 SVD fallbacks so far, [5] substeps recorded, [6] device error
+ * word, [7] grid pool capacity (blocks). */
+MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[8], void *stream);
+
+/* Diagnostic: P2G of the current state into dense device arrays m
+ * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at
+ * ((b * R0 + I) * R1 + J) * R2 + K) and mv (3 floats per node); the particle
+ * state is left unchanged.  Synchronises the stream. */
+MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream);
+
+/* Last error message of this context (or of the last failed mpm_create when
+ * ctx is NULL).  Static storage owned by the library. */
+MPM_API const char *mpm_last_error(const mpm_ctx *ctx);
+
+/* Frees every device buffer of the context; NULL-safe. */
+MPM_API mpm_status mpm_destroy(mpm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPM_H */

@@ -1,0 +1,153 @@
+"""ctypes binding of libmpm (include/mpm.h).  Same names as the C ABI; only
+argument marshalling happens here.  Importing this module fails loudly when
+the library has not been built: there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO = os.path.join(HERE, "_build", "libmpm.so")
+
+MPM_OK = 0
+STATUS_NAMES = {0: "MPM_OK", 1: "MPM_ERR_INVALID_ARG", 2: "MPM_ERR_OOM", 3: "MPM_ERR_CUDA",
+                4: "MPM_ERR_OUT_OF_DOMAIN", 5: "MPM_ERR_NONFINITE", 6: "MPM_ERR_TIMEOUT", 7: "MPM_ERR_STATE",
+                8: "MPM_ERR_CAPACITY", 9: "MPM_ERR_CFL"}
+
+
+class MpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class mpm_material(ctypes.Structure):
+    _fields_ = [("elastic", ctypes.c_int32), ("plastic", ctypes.c_int32), ("E", ctypes.c_float),
+                ("nu", ctypes.c_float), ("rho", ctypes.c_float), ("yield_stress", ctypes.c_float),
+                ("friction_angle_deg", ctypes.c_float)]
+
+
+class mpm_options(ctypes.Structure):
+    _fields_ = [("n_instances", ctypes.c_int32), ("bound", ctypes.c_int32), ("walls", ctypes.c_int32 * 6),
+                ("max_particles", ctypes.c_int64), ("max_active_blocks", ctypes.c_int64),
+                ("ckpt_every", ctypes.c_int32), ("chunk", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("scatter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_ctx_p = ctypes.c_void_p
+_vp = ctypes.c_void_p
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f32p = ctypes.POINTER(ctypes.c_float)
+
+# name -> (restype, argtypes); every symbol include/mpm.h declares
+SIGNATURES = {
+    "mpm_default_options": (ctypes.c_int, [ctypes.POINTER(mpm_options)]),
+    "mpm_create": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
+                                  ctypes.c_int32, ctypes.POINTER(mpm_options), ctypes.POINTER(_ctx_p)]),
+    "mpm_load_particles": (ctypes.c_int, [_ctx_p, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "mpm_step": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, _vp]),
+    "mpm_get_particles": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp, _vp, _vp]),
+    "mpm_backward": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, _vp, _vp, _vp, _vp]),
+    "mpm_record_reset": (ctypes.c_int, [_ctx_p]),
+    "mpm_sync": (ctypes.c_int, [_ctx_p, _vp]),
+    "mpm_stats": (ctypes.c_int, [_ctx_p, _i64p, _vp]),
+    "mpm_last_error": (ctypes.c_char_p, [_ctx_p]),
+    "mpm_destroy": (ctypes.c_int, [_ctx_p]),
+    "mpm_debug_p2g": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads libmpm.so (raising when it is missing or lacks a symbol)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO):
+            raise ImportError("libmpm.so is not built (%s); run paper_2602_01723_gb300.build.build() or "
+                              "__graft_entry__.build()" % SO)
+        L = ctypes.CDLL(SO)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(status, ctx=None):
+    if status != MPM_OK:
+        msg = lib().mpm_last_error(ctx)
+        raise MpmError(status, msg.decode() if msg else "")
+    return status
+
+
+# thin same-name wrappers -----------------------------------------------------
+
+def mpm_default_options():
+    o = mpm_options()
+    check(lib().mpm_default_options(ctypes.byref(o)))
+    return o
+
+
+def mpm_create(grid_res, dx, dt, gravity, table, opt=None):
+    res = (ctypes.c_int32 * 3)(*[int(r) for r in grid_res])
+    g = (ctypes.c_float * 3)(*[float(v) for v in gravity])
+    mats = (mpm_material * len(table))()
+    for i, t in enumerate(table):
+        mats[i] = mpm_material(int(t["elastic"]), int(t["plastic"]), float(t["E"]), float(t["nu"]),
+                               float(t["rho"]), float(t.get("yield_stress", 0.0)),
+                               float(t.get("friction_angle_deg", 30.0)))
+    out = _ctx_p()
+    st = lib().mpm_create(res, float(dx), float(dt), g, mats, len(table),
+                          ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+    check(st, None)
+    return out
+
+
+def mpm_load_particles(ctx, n, x, v, C, F, vol, material_id, instance, params, stream):
+    check(lib().mpm_load_particles(ctx, int(n), x, v, C, F, vol, material_id, instance, params, stream), ctx)
+
+
+def mpm_step(ctx, n_substeps, record, stream):
+    check(lib().mpm_step(ctx, int(n_substeps), int(record), stream), ctx)
+
+
+def mpm_get_particles(ctx, x, v, C, F, stream):
+    check(lib().mpm_get_particles(ctx, x, v, C, F, stream), ctx)
+
+
+def mpm_backward(ctx, frame_substep, dL_dx, dL_dparams, dL_dstate0, stream):
+    fs = (ctypes.c_int32 * len(frame_substep))(*[int(f) for f in frame_substep])
+    check(lib().mpm_backward(ctx, len(frame_substep), fs, dL_dx, dL_dparams, dL_dstate0, stream), ctx)
+
+
+def mpm_record_reset(ctx):
+    check(lib().mpm_record_reset(ctx), ctx)
+
+
+def mpm_sync(ctx, stream):
+    check(lib().mpm_sync(ctx, stream), ctx)
+
+
+def mpm_stats(ctx, stream):
+    c = (ctypes.c_int64 * 8)()
+    check(lib().mpm_stats(ctx, c, stream), ctx)
+    keys = ["particles", "occupied_blocks", "active_blocks", "chunks", "fp64_svd_fallbacks", "recorded",
+            "device_error", "pool_blocks"]
+    return dict(zip(keys, list(c)))
+
+
+def mpm_last_error(ctx):
+    m = lib().mpm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def mpm_destroy(ctx):
+    if ctx:
+        check(lib().mpm_destroy(ctx))
+
+
+def mpm_debug_p2g(ctx, m, mv, stream):
+    check(lib().mpm_debug_p2g(ctx, m, mv, stream), ctx)

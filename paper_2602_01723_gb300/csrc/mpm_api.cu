@@ -1,0 +1,495 @@
+// mpm_api.cu -- host side of libmpm: the C ABI declared in include/mpm.h.
+// Owns every device buffer, validates arguments, sequences the kernels of
+// mpm_forward.cu / mpm_adjoint.cu on the caller's stream and maps the sticky
+// device error word to mpm_status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_internal.h"
+
+using namespace mpm;
+
+namespace {
+
+const char *g_create_error = "";
+thread_local std::string g_create_msg;
+
+}  // namespace
+
+
+namespace {
+
+mpm_status fail(mpm_ctx *c, mpm_status s, const std::string &m) {
+    if (c) c->msg = m;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define CKLAUNCH()                                                                                \
+    do {                                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                                      \
+        if (e_ != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+mpm_status dalloc(mpm_ctx *ctx, T **p, size_t count, bool zero) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(ctx, e == cudaErrorMemoryAllocation ? MPM_ERR_OOM : MPM_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    if (zero) {
+        e = cudaMemset(*p, 0, count * sizeof(T));
+        if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("cudaMemset: ") + cudaGetErrorString(e));
+    }
+    return MPM_OK;
+}
+
+template <typename T> void dfree(T *&p) {
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+bool mpm::is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+mpm_status status_from_err(mpm_ctx *ctx, unsigned err) {
+    if (!err) return MPM_OK;
+    std::string m = "device error:";
+    mpm_status s = MPM_OK;
+    if (err & ERRB_DOMAIN) { m += " particle outside the grid stencil range or bad material/instance id;"; s = MPM_ERR_OUT_OF_DOMAIN; }
+    if (err & ERRB_NONFINITE) { m += " non-finite state or J <= 0 under Neo-Hookean;"; if (!s) s = MPM_ERR_NONFINITE; }
+    if (err & ERRB_CAPACITY) { m += " grid block pool or chunk list exhausted;"; if (!s) s = MPM_ERR_CAPACITY; }
+    if (err & ERRB_CFL) { m += " a particle moved more than one cell in a substep;"; if (!s) s = MPM_ERR_CFL; }
+    if (err & ERRB_TIMEOUT) { m += " bounded wait expired;"; if (!s) s = MPM_ERR_TIMEOUT; }
+    ctx->msg = m;
+    ctx->sticky = MPM_ERR_STATE;
+    return s;
+}
+
+mpm_status check_device_error(mpm_ctx *ctx, cudaStream_t st) {
+    CK(cudaStreamSynchronize(st));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, ctx->D.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    return status_from_err(ctx, err);
+}
+
+// copy a caller array to a device pointer usable by kernels (staging host data)
+mpm_status stage_in(mpm_ctx *ctx, const void *src, size_t bytes, size_t &off, const void **dev, cudaStream_t st) {
+    *dev = nullptr;
+    if (!src) return MPM_OK;
+    if (is_device_ptr(src)) { *dev = src; return MPM_OK; }
+    off = (off + 255) & ~size_t(255);
+    if (off + bytes > ctx->stage_bytes) return fail(ctx, MPM_ERR_CUDA, "internal: staging buffer too small");
+    void *d = (char *)ctx->stage + off;
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, st));
+    *dev = d;
+    off += bytes;
+    return MPM_OK;
+}
+
+mpm_status ensure_stage(mpm_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->stage_bytes) return MPM_OK;
+    dfree(ctx->stage);
+    ctx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->stage, bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); ctx->stage = nullptr; return fail(ctx, MPM_ERR_OOM, "staging allocation failed"); }
+    ctx->stage_bytes = bytes;
+    return MPM_OK;
+}
+
+mpm_status ensure_particles(mpm_ctx *ctx, long long n) {
+    if (n <= ctx->cap && ctx->D.rec) return MPM_OK;
+    long long cap = n;
+    if (ctx->opt.max_particles > cap) cap = ctx->opt.max_particles;
+    Dev &D = ctx->D;
+    mpm_status s;
+    if ((s = dalloc(ctx, &D.rec, (size_t)cap * REC_F4, false))) return s;
+    if ((s = dalloc(ctx, &D.key, (size_t)cap, false))) return s;
+    if ((s = dalloc(ctx, &D.rank, (size_t)cap, false))) return s;
+    if ((s = dalloc(ctx, &D.sorted, (size_t)cap, false))) return s;
+    ctx->cap = cap;
+    // grid pool: at most 27 active blocks per occupied block
+    unsigned long long occ_max = (unsigned long long)std::min<long long>(cap, ctx->total_blocks);
+    unsigned long long pool = ctx->opt.max_active_blocks > 0 ? (unsigned long long)ctx->opt.max_active_blocks
+                                                             : std::min<unsigned long long>(ctx->total_blocks, 27ull * occ_max);
+    if (pool > 0xffffffffull / BLK_NODES) pool = 0xffffffffull / BLK_NODES;
+    if (pool > ctx->pool_blocks) {
+        for (int k = 0; k < 2; ++k) {
+            if ((s = dalloc(ctx, &D.gmv[k], (size_t)pool * BLK_NODES, true))) return s;
+            if ((s = dalloc(ctx, &D.gv[k], (size_t)pool * BLK_NODES, true))) return s;
+            if ((s = dalloc(ctx, &D.active[k], (size_t)pool, false))) return s;
+        }
+        ctx->pool_blocks = (unsigned)pool;
+    }
+    D.max_active = ctx->pool_blocks;
+    unsigned long long chunks = (unsigned long long)(cap / D.chunk) + occ_max + 1;
+    if (chunks > ctx->chunk_cap) {
+        if ((s = dalloc(ctx, &D.chunks, (size_t)chunks, false))) return s;
+        ctx->chunk_cap = (unsigned)chunks;
+    }
+    D.max_chunks = ctx->chunk_cap;
+    // staging: inputs are at most 30 floats per particle
+    return ensure_stage(ctx, (size_t)cap * 30 * sizeof(float) + 16 * 256);
+}
+
+cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
+
+}  // namespace
+
+// ===========================================================================
+// internal sequencing shared with the adjoint translation unit
+// ===========================================================================
+namespace mpm {
+
+// forward of n substeps from the current state (bins must be valid);
+// leaves the state advanced and binned
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
+    Dev &D = ctx->D;
+    if (n_sub <= 0) return MPM_OK;
+    launch_plan(D, 0, st);
+    launch_activate_sort(D, 0, 1, ctx->grid_small, st);
+    launch_substep(D, 0, 0, 0, ctx->grid_sub[0], ctx->threads, st);
+    for (int s = 0; s < n_sub; ++s) {
+        int par = s & 1;
+        bool last = s == n_sub - 1;
+        launch_grid_update(D, par, last ? -1 : (par ^ 1), ctx->grid_small, st);
+        if (!last) {
+            launch_activate_sort(D, par ^ 1, 1, ctx->grid_small, st);
+            launch_substep(D, 1, par, par ^ 1, ctx->grid_sub[1], ctx->threads, st);
+            launch_plan(D, -1, st);
+        } else {
+            if (s > 0) launch_activate_sort(D, -1, 1, ctx->grid_small, st);   // sort for the latest plan
+            launch_substep(D, 2, par, 0, ctx->grid_sub[2], ctx->threads, st);
+        }
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return MPM_OK;
+}
+
+mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m) { return fail(ctx, s, m); }
+mpm_status ctx_check(mpm_ctx *ctx, cudaStream_t st) { return check_device_error(ctx, st); }
+
+}  // namespace mpm
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+MPM_API mpm_status mpm_default_options(mpm_options *opt) {
+    if (!opt) return MPM_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->n_instances = 1;
+    opt->bound = 3;
+    opt->walls[0] = MPM_WALL_SLIP;
+    opt->walls[1] = MPM_WALL_SLIP;
+    opt->walls[2] = MPM_WALL_STICKY;
+    opt->walls[3] = MPM_WALL_SLIP;
+    opt->walls[4] = MPM_WALL_SLIP;
+    opt->walls[5] = MPM_WALL_SLIP;
+    opt->ckpt_every = 20;
+    opt->scatter = 1;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, const float gravity[3],
+                              const mpm_material *table, int32_t n_materials, const mpm_options *opt,
+                              mpm_ctx **out) {
+    g_create_error = "";
+    if (!out) { g_create_error = "out is NULL"; return MPM_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (!grid_res || !gravity || !table || n_materials < 1) { g_create_error = "NULL argument or no materials"; return MPM_ERR_INVALID_ARG; }
+    for (int d = 0; d < 3; ++d)
+        if (grid_res[d] < 8 || grid_res[d] % 4 != 0 || grid_res[d] > 4096) {
+            g_create_error = "grid_res must be multiples of 4 in [8, 4096]";
+            return MPM_ERR_INVALID_ARG;
+        }
+    if (!(dx > 0.f) || !(dt > 0.f) || !std::isfinite(dx) || !std::isfinite(dt)) { g_create_error = "dx and dt must be positive"; return MPM_ERR_INVALID_ARG; }
+    mpm_options o;
+    mpm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.n_instances < 1 || o.bound < 0 || o.ckpt_every < 0 || o.scatter < 0 || o.scatter > 2 || o.chunk < 0) {
+        g_create_error = "bad options";
+        return MPM_ERR_INVALID_ARG;
+    }
+    if (o.ckpt_every == 0) o.ckpt_every = 20;
+    for (int i = 0; i < 6; ++i)
+        if (o.walls[i] < 0 || o.walls[i] > 2) { g_create_error = "bad wall type"; return MPM_ERR_INVALID_ARG; }
+    for (int m = 0; m < n_materials; ++m) {
+        const mpm_material &t = table[m];
+        if (t.elastic < 0 || t.elastic > 1 || t.plastic < 0 || t.plastic > 2 || !(t.E > 0.f) || !(t.rho > 0.f) ||
+            !(t.nu > -1.f && t.nu < 0.5f)) {
+            g_create_error = "bad material table entry";
+            return MPM_ERR_INVALID_ARG;
+        }
+    }
+    long long bpi = (long long)(grid_res[0] / 4) * (grid_res[1] / 4) * (grid_res[2] / 4);
+    long long total = bpi * o.n_instances;
+    if (total > (1ll << 31)) { g_create_error = "too many grid blocks"; return MPM_ERR_INVALID_ARG; }
+
+    mpm_ctx *ctx = new (std::nothrow) mpm_ctx();
+    if (!ctx) { g_create_error = "host allocation failed"; return MPM_ERR_OOM; }
+    cudaGetDevice(&ctx->device);
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
+    std::memset(&ctx->D, 0, sizeof(Dev));
+    Dev &D = ctx->D;
+    for (int d = 0; d < 3; ++d) {
+        ctx->R[d] = grid_res[d];
+        D.R[d] = grid_res[d];
+        D.NB[d] = grid_res[d] / 4;
+        ctx->g[d] = gravity[d];
+        D.g[d] = gravity[d];
+    }
+    D.bpi = (int)bpi;
+    D.n_inst = o.n_instances;
+    ctx->dx = dx; ctx->dt = dt;
+    D.dx = dx; D.inv_dx = 1.f / dx; D.dt = dt;
+    D.bound = o.bound;
+    for (int i = 0; i < 6; ++i) D.wall[i] = o.walls[i];
+    ctx->opt = o;
+    ctx->table.assign(table, table + n_materials);
+    ctx->total_blocks = total;
+    ctx->threads = 128;
+    D.chunk = o.chunk > 0 ? std::min(o.chunk, substep_chunk_max()) : 128;
+    mpm_status s = MPM_OK;
+#define CREATE_TRY(x)                              \
+    if ((s = (x)) != MPM_OK) {                     \
+        g_create_msg = ctx->msg;                   \
+        g_create_error = g_create_msg.c_str();     \
+        mpm_destroy(ctx);                          \
+        return s;                                  \
+    }
+    std::vector<float> E(n_materials), nu(n_materials), rho(n_materials), ys(n_materials), al(n_materials);
+    std::vector<int> el(n_materials), pl(n_materials);
+    for (int m = 0; m < n_materials; ++m) {
+        E[m] = table[m].E; nu[m] = table[m].nu; rho[m] = table[m].rho; ys[m] = table[m].yield_stress;
+        el[m] = table[m].elastic; pl[m] = table[m].plastic;
+        // Drucker-Prager alpha of the friction angle (Klar et al. 2016)
+        double sphi = std::sin(table[m].friction_angle_deg * M_PI / 180.0);
+        al[m] = (float)(std::sqrt(2.0 / 3.0) * 2.0 * sphi / (3.0 - sphi));
+    }
+    CREATE_TRY(dalloc(ctx, &ctx->mE, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->mnu, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->mrho, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->myield, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->malpha, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->mel, n_materials, false));
+    CREATE_TRY(dalloc(ctx, &ctx->mpl, n_materials, false));
+    cudaMemcpy(ctx->mE, E.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->mnu, nu.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->mrho, rho.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->myield, ys.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->malpha, al.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->mel, el.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    cudaMemcpy(ctx->mpl, pl.data(), n_materials * 4, cudaMemcpyHostToDevice);
+    for (int k = 0; k < 2; ++k) {
+        CREATE_TRY(dalloc(ctx, &D.page[k], (size_t)total, false));
+        CREATE_TRY(dalloc(ctx, &D.page_epoch[k], (size_t)total, true));
+    }
+    CREATE_TRY(dalloc(ctx, &D.bcount, (size_t)total, true));
+    CREATE_TRY(dalloc(ctx, &D.bstart, (size_t)total, false));
+    CREATE_TRY(dalloc(ctx, &D.occ, (size_t)total, false));
+    CREATE_TRY(dalloc(ctx, &D.plan, (size_t)total, false));
+    CREATE_TRY(dalloc(ctx, &D.ctr, CTR_COUNT, true));
+    CREATE_TRY(dalloc(ctx, &D.err, 1, true));
+    D.scatter = o.scatter;
+    for (int m = 0; m < 3; ++m) {
+        int occ = substep_occupancy(m, D.scatter, ctx->threads);
+        ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
+    }
+    ctx->grid_small = ctx->sm_count * 8;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        g_create_msg = std::string("create: ") + cudaGetErrorString(e);
+        g_create_error = g_create_msg.c_str();
+        mpm_destroy(ctx);
+        return MPM_ERR_CUDA;
+    }
+    *out = ctx;
+    return MPM_OK;
+#undef CREATE_TRY
+}
+
+MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, const float *v, const float *C,
+                                      const float *F, const float *vol, const int32_t *material_id,
+                                      const int32_t *instance, const float *params, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (n <= 0 || n > (1ll << 31) - 1 || !x || !vol || !material_id)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "n must be in [1, 2^31) and x, vol, material_id non-NULL");
+    cudaStream_t st = S(stream);
+    mpm_status s = ensure_particles(ctx, n);
+    if (s) return s;
+    Dev &D = ctx->D;
+    D.n = (int)n;
+    size_t off = 0;
+    LoadArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const void *p;
+    if ((s = stage_in(ctx, x, n * 12, off, &p, st))) return s; a.x = (const float *)p;
+    if ((s = stage_in(ctx, v, n * 12, off, &p, st))) return s; a.v = (const float *)p;
+    if ((s = stage_in(ctx, C, n * 36, off, &p, st))) return s; a.C = (const float *)p;
+    if ((s = stage_in(ctx, F, n * 36, off, &p, st))) return s; a.F = (const float *)p;
+    if ((s = stage_in(ctx, vol, n * 4, off, &p, st))) return s; a.vol = (const float *)p;
+    if ((s = stage_in(ctx, material_id, n * 4, off, &p, st))) return s; a.mat = (const int *)p;
+    if ((s = stage_in(ctx, instance, n * 4, off, &p, st))) return s; a.inst = (const int *)p;
+    if ((s = stage_in(ctx, params, n * 12, off, &p, st))) return s; a.params = (const float *)p;
+    a.table = MatTable{(int)ctx->table.size(), ctx->mE, ctx->mnu, ctx->mrho, ctx->myield, ctx->malpha, ctx->mel, ctx->mpl};
+    CK(cudaMemsetAsync(D.err, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(D.bcount, 0, (size_t)ctx->total_blocks * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(D.ctr + CTR_N_OCC, 0, sizeof(unsigned), st));
+    launch_load(D, a, st);
+    launch_bin(D, st);
+    CKLAUNCH();
+    ctx->sticky = MPM_OK;
+    ctx->loaded = true;
+    ctx->recorded = 0;
+    ctx->record_broken = false;
+    s = check_device_error(ctx, st);
+    if (s) ctx->loaded = false;
+    return s;
+}
+
+MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (n_substeps < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "n_substeps < 0");
+    if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state (load particles first)");
+    if (n_substeps == 0) return MPM_OK;
+    cudaStream_t st = S(stream);
+    if (!record) {
+        if (ctx->recorded > 0) ctx->record_broken = true;
+        return run_substeps(ctx, n_substeps, st);
+    }
+    return record_substeps(ctx, n_substeps, st);
+}
+
+MPM_API mpm_status mpm_get_particles(mpm_ctx *ctx, float *x, float *v, float *C, float *F, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    cudaStream_t st = S(stream);
+    Dev &D = ctx->D;
+    size_t n = (size_t)D.n;
+    float *outs[4] = {x, v, C, F};
+    size_t widths[4] = {3, 3, 9, 9};
+    float *dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t off = 0;
+    for (int i = 0; i < 4; ++i) {
+        if (!outs[i]) continue;
+        if (is_device_ptr(outs[i])) { dptr[i] = outs[i]; continue; }
+        off = (off + 255) & ~size_t(255);
+        dptr[i] = (float *)((char *)ctx->stage + off);
+        off += n * widths[i] * sizeof(float);
+    }
+    if (off > ctx->stage_bytes) return fail(ctx, MPM_ERR_CUDA, "internal: staging too small");
+    launch_export(D, dptr[0], dptr[1], dptr[2], dptr[3], st);
+    CKLAUNCH();
+    for (int i = 0; i < 4; ++i)
+        if (outs[i] && dptr[i] != outs[i])
+            CK(cudaMemcpyAsync(outs[i], dptr[i], n * widths[i] * sizeof(float), cudaMemcpyDeviceToHost, st));
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    return check_device_error(ctx, S(stream));
+}
+
+MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[8], void *stream) {
+    if (!ctx || !counters) return MPM_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    CK(cudaStreamSynchronize(st));
+    unsigned c[CTR_COUNT], err = 0;
+    CK(cudaMemcpy(c, ctx->D.ctr, sizeof(c), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&err, ctx->D.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    counters[0] = ctx->D.n;
+    counters[1] = c[CTR_N_PLAN];
+    counters[2] = std::max(c[CTR_N_ACTIVE], c[CTR_N_ACTIVE + 1]);
+    counters[3] = c[CTR_N_CHUNKS];
+    counters[4] = c[CTR_FALLBACKS];
+    counters[5] = ctx->recorded;
+    counters[6] = err;
+    counters[7] = ctx->pool_blocks;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_record_reset(mpm_ctx *ctx) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    ctx->recorded = 0;
+    ctx->record_broken = false;
+    return MPM_OK;
+}
+
+MPM_API const char *mpm_last_error(const mpm_ctx *ctx) {
+    if (!ctx) return g_create_error;
+    return ctx->msg.c_str();
+}
+
+MPM_API mpm_status mpm_destroy(mpm_ctx *ctx) {
+    if (!ctx) return MPM_OK;
+    Dev &D = ctx->D;
+    dfree(D.rec); dfree(D.key); dfree(D.rank); dfree(D.sorted); dfree(D.bcount); dfree(D.bstart);
+    dfree(D.occ); dfree(D.plan); dfree(D.chunks); dfree(D.ctr); dfree(D.err);
+    for (int k = 0; k < 2; ++k) {
+        dfree(D.page[k]); dfree(D.page_epoch[k]); dfree(D.active[k]); dfree(D.gmv[k]); dfree(D.gv[k]);
+    }
+    dfree(ctx->mE); dfree(ctx->mnu); dfree(ctx->mrho); dfree(ctx->myield); dfree(ctx->malpha);
+    dfree(ctx->mel); dfree(ctx->mpl);
+    dfree(ctx->stage);
+    free_adjoint(ctx->adj);
+    delete ctx;
+    return MPM_OK;
+}
+
+// P2G of the current state into dense caller arrays m (n_inst*R0*R1*R2) and
+// mv (x3); the particle state is left unchanged.  Diagnostic entry point used
+// by the teacher-forced parity tests.
+MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream) {
+    if (!ctx || !m || !mv) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state");
+    if (!is_device_ptr(m) || !is_device_ptr(mv)) return fail(ctx, MPM_ERR_INVALID_ARG, "m, mv must be device arrays");
+    cudaStream_t st = S(stream);
+    Dev &D = ctx->D;
+    size_t nn = (size_t)ctx->total_blocks * BLK_NODES;
+    CK(cudaMemsetAsync(m, 0, nn * sizeof(float), st));
+    CK(cudaMemsetAsync(mv, 0, 3 * nn * sizeof(float), st));
+    launch_plan(D, 0, st);
+    launch_activate_sort(D, 0, 1, ctx->grid_small, st);
+    launch_substep(D, 0, 0, 0, ctx->grid_sub[0], ctx->threads, st);
+    launch_grid_dense(D, 0, 0, m, mv, st);
+    // clear the momentum buffer again (the update zeroes it); the binning of
+    // the current positions was consumed by the plan, so rebuild it
+    launch_grid_update(D, 0, -1, ctx->grid_small, st);
+    launch_bin(D, st);
+    CKLAUNCH();
+    return check_device_error(ctx, st);
+}
+
+}  // extern "C"

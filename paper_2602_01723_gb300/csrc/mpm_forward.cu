@@ -1,0 +1,769 @@
+// mpm_forward.cu -- forward kernels of the MLS-MPM substep.
+//
+// Pipeline of one call advancing S substeps (grid buffers alternate by
+// parity; particles are grouped by their 4x4x4 grid block at the start):
+//   plan -> activate/sort -> P2G(x_0)
+//   repeat: grid update(s) -> [activate(s+1) -> G2P(s) fused with P2G(s+1)
+//           -> plan -> sort]            ... last substep: G2P(S-1) only
+// The fused kernel reads each particle once per substep: it gathers the
+// grid velocity at x_s, updates x, v, C, F (and applies the return map),
+// evaluates the stress of the new F and scatters mass and momentum at x_{s+1}
+// into a shared-memory tile, then bins the particle for the next substep.
+#include "mpm_dev.cuh"
+#include "mpm_internal.h"
+#include "mpm_math.cuh"
+
+namespace mpm {
+
+// ---------------------------------------------------------------------------
+// particle load: caller arrays -> records
+// ---------------------------------------------------------------------------
+__global__ void k_load(Dev D, const float *__restrict__ x, const float *__restrict__ v, const float *__restrict__ C,
+                       const float *__restrict__ F, const float *__restrict__ vol, const int *__restrict__ mat,
+                       const int *__restrict__ inst, const float *__restrict__ params, MatTable T) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < D.n; p += gridDim.x * blockDim.x) {
+        int m = mat[p];
+        int in = inst ? inst[p] : 0;
+        if (m < 0 || m >= T.n || in < 0 || in >= D.n_inst) {
+            set_err(D, ERRB_DOMAIN);
+            m = m < 0 ? 0 : (m >= T.n ? T.n - 1 : m);
+            in = in < 0 ? 0 : (in >= D.n_inst ? D.n_inst - 1 : in);
+        }
+        float E = T.E[m], nu = T.nu[m], ys = T.yield[m];
+        if (params) {
+            E = expf(params[3 * p]);
+            nu = params[3 * p + 1];
+            ys = params[3 * p + 2];
+        }
+        // Lame parameters (App. B.1)
+        float mu = E / (2.f * (1.f + nu));
+        float lam = E * nu / ((1.f + nu) * (1.f - 2.f * nu));
+        float vp = vol[p];
+        float c[9], f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            c[i] = C ? C[9 * p + i] : 0.f;
+            f[i] = F ? F[9 * p + i] : ((i % 4 == 0) ? 1.f : 0.f);
+        }
+        int info = T.elastic[m] | (T.plastic[m] << 4) | (m << 8);
+        float4 *r = D.rec + (size_t)p * REC_F4;
+        r[0] = make_float4(x[3 * p], x[3 * p + 1], x[3 * p + 2], T.rho[m] * vp);
+        r[1] = v ? make_float4(v[3 * p], v[3 * p + 1], v[3 * p + 2], vp) : make_float4(0.f, 0.f, 0.f, vp);
+        r[2] = make_float4(c[0], c[1], c[2], c[3]);
+        r[3] = make_float4(c[4], c[5], c[6], c[7]);
+        r[4] = make_float4(c[8], f[0], f[1], f[2]);
+        r[5] = make_float4(f[3], f[4], f[5], f[6]);
+        r[6] = make_float4(f[7], f[8], mu, lam);
+        r[7] = make_float4(ys, __int_as_float(info), __int_as_float(in), T.alpha[m]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// binning helpers
+// ---------------------------------------------------------------------------
+
+// Particle block key from its position; false when the stencil leaves the grid.
+__device__ __forceinline__ bool particle_key(const Dev &D, float x0, float x1, float x2, int inst, unsigned &key) {
+    float f;
+    int b0 = base_cell(x0, D.inv_dx, f), b1 = base_cell(x1, D.inv_dx, f), b2 = base_cell(x2, D.inv_dx, f);
+    bool ok = b0 >= 0 && b1 >= 0 && b2 >= 0 && b0 <= D.R[0] - 3 && b1 <= D.R[1] - 3 && b2 <= D.R[2] - 3;
+    if (!ok) {   // keep the index in range; the error bit makes the result void
+        b0 = min(max(b0, 0), D.R[0] - 3);
+        b1 = min(max(b1, 0), D.R[1] - 3);
+        b2 = min(max(b2, 0), D.R[2] - 3);
+    }
+    key = block_key(D, inst, b0 >> 2, b1 >> 2, b2 >> 2);
+    return ok;
+}
+
+// Warp-aggregated counting: lanes with equal keys share one atomic; the first
+// particle of a block appends the block to the occupied list.  All lanes in
+// `mask` must call both halves together.  bin_begin issues the atomic;
+// bin_end consumes its result, so work placed between them hides its latency.
+struct BinTicket {
+    unsigned peers, base, key;
+};
+__device__ __forceinline__ BinTicket bin_begin(const Dev &D, unsigned mask, unsigned key) {
+    BinTicket t;
+    t.key = key;
+    t.peers = __match_any_sync(mask, key);
+    t.base = 0;
+    if ((int)(threadIdx.x & 31) == __ffs(t.peers) - 1) t.base = atomicAdd(&D.bcount[key], (unsigned)__popc(t.peers));
+    return t;
+}
+__device__ __forceinline__ void bin_end(const Dev &D, const BinTicket &t, unsigned p) {
+    const int leader = __ffs(t.peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader && t.base == 0) {
+        unsigned slot = atomicAdd(&D.ctr[CTR_N_OCC], 1u);
+        D.occ[slot] = t.key;
+    }
+    const unsigned base = __shfl_sync(t.peers, t.base, leader);
+    D.key[p] = t.key;
+    D.rank[p] = base + __popc(t.peers & lanemask_lt());
+}
+__device__ __forceinline__ void bin_particle(const Dev &D, unsigned mask, unsigned p, unsigned key) {
+    BinTicket t = bin_begin(D, mask, key);
+    bin_end(D, t, p);
+}
+
+__global__ void k_bin(Dev D) {
+    int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < D.n; p0 += stride) {
+        int p = p0 + threadIdx.x;
+        bool valid = p < D.n;
+        unsigned mask = __ballot_sync(0xffffffffu, valid);
+        if (!valid) continue;
+        float4 r0 = D.rec[(size_t)p * REC_F4];
+        int inst = __float_as_int(D.rec[(size_t)p * REC_F4 + 7].z);
+        unsigned key;
+        if (!particle_key(D, r0.x, r0.y, r0.z, inst, key)) set_err(D, ERRB_DOMAIN);
+        bin_particle(D, mask, (unsigned)p, key);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plan: one CTA scans the occupied blocks -> block starts and work chunks
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void block_scan2(unsigned a, unsigned b, unsigned &ea, unsigned &eb, unsigned &ta,
+                                            unsigned &tb, unsigned *sh) {
+    // exclusive scan of (a, b) over a 1024-thread CTA; sh: 64 unsigned
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned ia = a, ib = b;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned ya = __shfl_up_sync(0xffffffffu, ia, o), yb = __shfl_up_sync(0xffffffffu, ib, o);
+        if (lane >= o) { ia += ya; ib += yb; }
+    }
+    if (lane == 31) { sh[w] = ia; sh[32 + w] = ib; }
+    __syncthreads();
+    if (w == 0) {
+        unsigned sa = sh[lane], sb = sh[32 + lane];
+        unsigned xa = sa, xb = sb;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned ya = __shfl_up_sync(0xffffffffu, xa, o), yb = __shfl_up_sync(0xffffffffu, xb, o);
+            if (lane >= o) { xa += ya; xb += yb; }
+        }
+        sh[lane] = xa - sa;
+        sh[32 + lane] = xb - sb;
+        if (lane == 31) { sh[64] = xa; sh[65] = xb; }
+    }
+    __syncthreads();
+    ea = sh[w] + ia - a;
+    eb = sh[32 + w] + ib - b;
+    ta = sh[64];
+    tb = sh[65];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_par) {
+    __shared__ unsigned sh[66];
+    const unsigned n = D.ctr[CTR_N_OCC];
+    const unsigned CH = (unsigned)D.chunk;
+    unsigned total = 0, tchunks = 0;
+    for (unsigned b0 = 0; b0 < n; b0 += blockDim.x) {
+        unsigned i = b0 + threadIdx.x;
+        unsigned key = 0, cnt = 0;
+        if (i < n) {
+            key = D.occ[i];
+            cnt = D.bcount[key];
+        }
+        unsigned nch = (cnt + CH - 1) / CH;
+        unsigned ec, ek, tc, tk;
+        block_scan2(cnt, nch, ec, ek, tc, tk, sh);
+        if (i < n) {
+            unsigned start = total + ec;
+            D.bstart[key] = start;
+            D.plan[i] = key;
+            D.bcount[key] = 0;
+            for (unsigned j = 0; j < nch; ++j) {
+                unsigned ci = tchunks + ek + j;
+                if (ci < D.max_chunks) D.chunks[ci] = make_int4((int)key, (int)(start + j * CH), (int)min(CH, cnt - j * CH), 0);
+                else set_err(D, ERRB_CAPACITY);
+            }
+        }
+        total += tc;
+        tchunks += tk;
+    }
+    if (threadIdx.x == 0) {
+        D.ctr[CTR_N_PLAN] = n;
+        D.ctr[CTR_N_CHUNKS] = min(tchunks, D.max_chunks);
+        D.ctr[CTR_N_OCC] = 0;
+        if (bump_par >= 0) {
+            unsigned e = D.ctr[CTR_EPOCH] + 1;
+            D.ctr[CTR_EPOCH] = e;
+            D.ctr[CTR_EPOCH_OF + bump_par] = e;
+            D.ctr[CTR_N_ACTIVE + bump_par] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// activate the 3x3x3 block neighbourhood of every occupied block in grid
+// buffer `par` (par < 0: no activation), and write the sorted particle index
+// ---------------------------------------------------------------------------
+__global__ void k_activate_sort(Dev D, int par, int do_sort) {
+    const unsigned nplan = D.ctr[CTR_N_PLAN];
+    const unsigned ep = par >= 0 ? D.ctr[CTR_EPOCH_OF + par] : 0u;
+    const unsigned items = par >= 0 ? nplan * 27u : 0u;
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    for (unsigned i = tid; i < items; i += stride) {
+        unsigned b = i / 27u, o = i - b * 27u;
+        int inst, bx, by, bz;
+        key_coords(D, D.plan[b], inst, bx, by, bz);
+        int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
+        if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
+        unsigned nk = block_key(D, inst, nx, ny, nz);
+        unsigned old = atomicMax(&D.page_epoch[par][nk], ep);
+        if (old != ep) {
+            unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + par], 1u);
+            if (slot < D.max_active) {
+                D.page[par][nk] = (int)slot;
+                D.active[par][slot] = nk;
+            } else {
+                D.page[par][nk] = -1;
+                set_err(D, ERRB_CAPACITY);
+            }
+        }
+    }
+    if (do_sort)
+        for (unsigned p = tid; p < (unsigned)D.n; p += stride) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
+}
+
+// ---------------------------------------------------------------------------
+// grid update (App. A): v = mv/m + dt g for m > 0, then walls; clears the
+// momentum buffer for its next use
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void apply_walls(const Dev &D, int I, int J, int K, float &u0, float &u1, float &u2) {
+    int idx[3] = {I, J, K};
+    bool sticky = false;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (idx[d] < D.bound && D.wall[2 * d] == 2) sticky = true;
+        if (idx[d] >= D.R[d] - D.bound && D.wall[2 * d + 1] == 2) sticky = true;
+    }
+    if (sticky) { u0 = u1 = u2 = 0.f; return; }
+    float *u[3] = {&u0, &u1, &u2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (idx[d] < D.bound && D.wall[2 * d] == 1 && *u[d] < 0.f) *u[d] = 0.f;
+        if (idx[d] >= D.R[d] - D.bound && D.wall[2 * d + 1] == 1 && *u[d] > 0.f) *u[d] = 0.f;
+    }
+}
+
+__global__ void k_grid_update(Dev D, int par, int bump_par, int keep_momentum) {
+    const unsigned total = D.ctr[CTR_N_ACTIVE + par] * BLK_NODES;
+    if (bump_par >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        // open a fresh epoch for the grid buffer activated next (not read here)
+        unsigned e = D.ctr[CTR_EPOCH] + 1;
+        D.ctr[CTR_EPOCH] = e;
+        D.ctr[CTR_EPOCH_OF + bump_par] = e;
+        D.ctr[CTR_N_ACTIVE + bump_par] = 0;
+    }
+    const unsigned lim = min(total, D.max_active * BLK_NODES);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
+        unsigned slot = i >> 6, l = i & 63u;
+        int inst, bx, by, bz;
+        key_coords(D, D.active[par][slot], inst, bx, by, bz);
+        int I = bx * BLK + (int)(l >> 4), J = by * BLK + (int)((l >> 2) & 3u), K = bz * BLK + (int)(l & 3u);
+        float4 a = D.gmv[par][i];
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.w > 0.f) {
+            float im = 1.f / a.w;
+            float u0 = a.x * im + D.dt * D.g[0], u1 = a.y * im + D.dt * D.g[1], u2 = a.z * im + D.dt * D.g[2];
+            apply_walls(D, I, J, K, u0, u1, u2);
+            out = make_float4(u0, u1, u2, a.w);
+        }
+        D.gv[par][i] = out;
+        if (!keep_momentum) D.gmv[par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the substep kernel
+//   MODE_P2G: scatter at the current positions (first substep of a call)
+//   MODE_FUSED: G2P(s) + update + return map + stress + P2G(s+1) + binning
+//   MODE_G2P: G2P(s) + update + return map + binning (last substep)
+//
+// One CTA works on one chunk (<= CH particles of one 4^3-node block) at a
+// time:
+//   0. the chunk's records are staged in shared memory by cooperative float4
+//      loads (many requests in flight instead of one dependent chain per
+//      thread), and the grid velocities of the block's 6^3-node gather tile
+//      are loaded;
+//   A. per particle: gather v and C (App. A G2P), x += dt v, F <- (I + dt C) F,
+//      one SVD serving the return map and the next stress, Kirchhoff stress,
+//      affine momentum A = m C - 4 dt V tau / dx^2 (§4.2); the new record goes
+//      to global memory and a 16-float scatter packet replaces the staged
+//      record; the particle is binned for the next substep;
+//   B. packets are scattered into the 8^3-node tile (nodes 4B-1 .. 4B+6) and
+//      the tile is flushed with one vector reduction per touched node.
+// SCAT selects the scatter of phase B: 0 = float shared-memory atomics;
+// 1 = int32 fixed-point shared-memory atomics with a per-chunk scale (native
+// integer atomics; the scale keeps the rounding below 2^-30 of the chunk's
+// total per quantity); 2 = vector reductions straight into the global grid.
+// ---------------------------------------------------------------------------
+enum { MODE_P2G = 0, MODE_FUSED = 1, MODE_G2P = 2 };
+
+constexpr int GT = 6;    // gather tile edge (nodes 4B .. 4B+5)
+constexpr int GT3 = GT * GT * GT;
+constexpr int ST = 8;    // scatter tile edge (nodes 4B-1 .. 4B+6)
+constexpr int ST3 = ST * ST * ST;
+constexpr int CH_MAX = 256;   // particles per chunk (records staged in shared memory)
+constexpr int SUB_THREADS = 128;
+
+__device__ __forceinline__ int page_slot(const Dev &D, int par, unsigned ep, int inst, int bx, int by, int bz) {
+    if (bx < 0 || by < 0 || bz < 0 || bx >= D.NB[0] || by >= D.NB[1] || bz >= D.NB[2]) return -1;
+    unsigned k = block_key(D, inst, bx, by, bz);
+    return D.page_epoch[par][k] == ep ? D.page[par][k] : -1;
+}
+
+__device__ __forceinline__ int node_local(int I, int J, int K) { return ((I & 3) * 4 + (J & 3)) * 4 + (K & 3); }
+
+struct SubstepSmem {
+    float4 rec[CH_MAX * REC_F4];     // staged records, then scatter packets (4 float4 each)
+    float4 g[GT3];                   // gather tile: (v, m) per node
+    union {
+        float f[4 * ST3];            // scatter tile, component-major [m0 | m1 | m2 | m]
+        int i[4 * ST3];
+    } t;
+    unsigned idx[CH_MAX];            // particle index of each chunk slot
+    int slot_s[27];                  // pool slot of blocks (B-1 .. B+1)^3 in the scatter grid
+    int slot_g[8];                   // pool slot of blocks (B .. B+1)^3 in the gather grid
+    float red[2 * (SUB_THREADS / 32)];
+    float scale[2];
+};
+
+template <int MODE, int SCAT>
+__global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int spar) {
+    extern __shared__ float4 smem_raw[];
+    SubstepSmem &S = *reinterpret_cast<SubstepSmem *>(smem_raw);
+    constexpr bool GATHER = MODE != MODE_P2G;
+    constexpr bool SCATTER = MODE != MODE_G2P;
+    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    const unsigned ep_g = GATHER ? D.ctr[CTR_EPOCH_OF + gpar] : 0u;
+    const unsigned ep_s = SCATTER ? D.ctr[CTR_EPOCH_OF + spar] : 0u;
+    const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
+    const int tid = threadIdx.x, T = blockDim.x;
+
+    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const int4 ch = D.chunks[c];
+        const int cnt = min(ch.z, CH_MAX);
+        int inst, bx, by, bz;
+        key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+        const int ox = bx * BLK, oy = by * BLK, oz = bz * BLK;   // gather tile origin (node)
+
+        // ---- 0. staging ---------------------------------------------------
+        for (int j = tid; j < cnt; j += T) S.idx[j] = D.sorted[ch.y + j];
+        if (SCATTER && tid < 27)
+            S.slot_s[tid] = page_slot(D, spar, ep_s, inst, bx + tid / 9 - 1, by + (tid / 3) % 3 - 1, bz + tid % 3 - 1);
+        if (GATHER && tid < 8)
+            S.slot_g[tid] = page_slot(D, gpar, ep_g, inst, bx + (tid >> 2), by + ((tid >> 1) & 1), bz + (tid & 1));
+        if (SCATTER && SCAT != 2)
+            for (int t = tid; t < 4 * ST3; t += T) S.t.i[t] = 0;
+        __syncthreads();
+        for (int q = tid; q < cnt * REC_F4; q += T) {
+            const int j = q >> 3, w = q & 7;
+            if (GATHER && (w == 2 || w == 3)) continue;   // the old C is not read by G2P
+            S.rec[q] = D.rec[(size_t)S.idx[j] * REC_F4 + w];
+        }
+        if (GATHER)
+            for (int t = tid; t < GT3; t += T) {
+                const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+                const int sl = S.slot_g[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+                S.g[t] = sl >= 0 ? D.gv[gpar][(size_t)sl * BLK_NODES + node_local(i, j, k)]
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        __syncthreads();
+
+        // ---- A. per-particle update -----------------------------------------
+        float bnd_m = 0.f, bnd_v = 0.f;
+        const int rounds = (cnt + T - 1) / T;
+        for (int r = 0; r < rounds; ++r) {
+            const int j = r * T + tid;
+            const bool valid = j < cnt;
+            const unsigned lane_mask = __ballot_sync(0xffffffffu, valid);
+            if (!valid) continue;
+            const unsigned p = S.idx[j];
+            float4 *sr = S.rec + j * REC_F4;
+            const float4 r0 = sr[0], r1 = sr[1], r6 = sr[6], r7 = sr[7];
+            float x[3] = {r0.x, r0.y, r0.z};
+            const float mass = r0.w, vol = r1.w;
+            float v[3] = {r1.x, r1.y, r1.z};
+            const float mu = r6.z, lam = r6.w, yield = r7.x;
+            const int info = __float_as_int(r7.y);
+            const int elastic = info & 15, plastic = (info >> 4) & 15;
+            float F[9], Cm[9], U[9], s3[3], e3[3];
+            {
+                const float4 r4 = sr[4], r5 = sr[5];
+                F[0] = r4.y; F[1] = r4.z; F[2] = r4.w; F[3] = r5.x; F[4] = r5.y; F[5] = r5.z; F[6] = r5.w;
+                F[7] = r6.x; F[8] = r6.y;
+                Cm[8] = r4.x;
+            }
+            float4 *rp = D.rec + (size_t)p * REC_F4;
+            unsigned key = 0;
+            bool in_dom = true;
+            BinTicket ticket;
+            if (GATHER) {
+                float f0, f1, f2;
+                int b0 = base_cell(x[0], inv_dx, f0) - ox, b1 = base_cell(x[1], inv_dx, f1) - oy,
+                    b2 = base_cell(x[2], inv_dx, f2) - oz;
+                if ((unsigned)b0 > 3u || (unsigned)b1 > 3u || (unsigned)b2 > 3u) {   // grouping invariant broken
+                    set_err(D, ERRB_CFL);
+                    b0 = min(max(b0, 0), 3); b1 = min(max(b1, 0), 3); b2 = min(max(b2, 0), 3);
+                }
+                float w0[3], w1[3], w2[3];
+                bspline_w(f0, w0);
+                bspline_w(f1, w1);
+                bspline_w(f2, w2);
+                float vn[3] = {0.f, 0.f, 0.f};
+                float Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float d0 = (float)i - f0;
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float d1 = (float)jj - f1;
+                        const float wij = w0[i] * w1[jj];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float d2 = (float)k - f2;
+                            const float wt = wij * w2[k];
+                            const float4 g = S.g[((b0 + i) * GT + (b1 + jj)) * GT + (b2 + k)];
+                            const float a0 = wt * g.x, a1 = wt * g.y, a2 = wt * g.z;
+                            vn[0] += a0; vn[1] += a1; vn[2] += a2;
+                            Bm[0] += a0 * d0; Bm[1] += a0 * d1; Bm[2] += a0 * d2;
+                            Bm[3] += a1 * d0; Bm[4] += a1 * d1; Bm[5] += a1 * d2;
+                            Bm[6] += a2 * d0; Bm[7] += a2 * d1; Bm[8] += a2 * d2;
+                        }
+                    }
+                }
+                // C = 4/dx^2 sum w v (x_i - x_p)^T with (x_i - x_p) = (o - f) dx
+                const float cs = 4.f * inv_dx;
+#pragma unroll
+                for (int t = 0; t < 9; ++t) Cm[t] = cs * Bm[t];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) { v[d] = vn[d]; x[d] += dt * vn[d]; }
+                in_dom = particle_key(D, x[0], x[1], x[2], inst, key);
+                ticket = bin_begin(D, lane_mask, key);      // result consumed after the SVD
+                rp[1] = make_float4(v[0], v[1], v[2], vol);
+                rp[2] = make_float4(Cm[0], Cm[1], Cm[2], Cm[3]);
+                rp[3] = make_float4(Cm[4], Cm[5], Cm[6], Cm[7]);
+                // F <- (I + dt C) F
+                float G[9];
+#pragma unroll
+                for (int rr = 0; rr < 3; ++rr)
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        G[3 * rr + cc] = F[3 * rr + cc] + dt * (Cm[3 * rr] * F[cc] + Cm[3 * rr + 1] * F[3 + cc] +
+                                                                Cm[3 * rr + 2] * F[6 + cc]);
+                // one SVD of the updated F serves the return map and the next stress
+                if (plastic != PLASTIC_NONE || (SCATTER && elastic == 0)) {
+                    float Vv[9], d3[3];
+                    const int fb = svd3_robust(G, U, Vv, s3, e3, d3);
+                    if (fb) {
+                        atomicAdd(&D.ctr[CTR_FALLBACKS], 1u);
+                        if (fb == 2) set_err(D, ERRB_NONFINITE);
+                    }
+                    if (plastic != PLASTIC_NONE) {
+                        const float alpha = r7.w;
+                        float z[3], ze[3];
+                        const int rm = return_map(plastic, s3, e3, d3, mu, lam, yield, alpha, z, ze);
+                        if (rm != RM_ELASTIC) {
+                            usvt(G, U, z, Vv);
+#pragma unroll
+                            for (int t = 0; t < 3; ++t) { s3[t] = z[t]; e3[t] = ze[t]; }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int t = 0; t < 9; ++t) F[t] = G[t];
+                if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) set_err(D, ERRB_NONFINITE);
+                rp[0] = make_float4(x[0], x[1], x[2], mass);
+                rp[4] = make_float4(Cm[8], F[0], F[1], F[2]);
+                rp[5] = make_float4(F[3], F[4], F[5], F[6]);
+                rp[6] = make_float4(F[7], F[8], mu, lam);
+            } else {
+                const float4 r2 = sr[2], r3 = sr[3];
+                Cm[0] = r2.x; Cm[1] = r2.y; Cm[2] = r2.z; Cm[3] = r2.w;
+                Cm[4] = r3.x; Cm[5] = r3.y; Cm[6] = r3.z; Cm[7] = r3.w;
+                if (elastic == 0) {
+                    float Vv[9], d3[3];
+                    const int fb = svd3_robust(F, U, Vv, s3, e3, d3);
+                    if (fb) {
+                        atomicAdd(&D.ctr[CTR_FALLBACKS], 1u);
+                        if (fb == 2) set_err(D, ERRB_NONFINITE);
+                    }
+                }
+            }
+
+            if (!GATHER) in_dom = particle_key(D, x[0], x[1], x[2], inst, key);
+            if (!in_dom) set_err(D, ERRB_DOMAIN);
+
+            if (SCATTER) {
+                // Kirchhoff stress of F (App. B.1 / App. A) and the affine momentum
+                // A = m C - 4 dt V / dx^2 tau of the §4.2 equation, as Ad = A dx
+                Sym tau;
+                if (elastic == 0) {
+                    tau = tau_fcr(U, s3, e3, mu, lam);
+                } else if (!tau_nh(F, mu, lam, tau)) {
+                    set_err(D, ERRB_NONFINITE);
+                    tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                }
+                const float kf = 4.f * dt * vol * inv_dx * inv_dx;
+                float Ad[9];
+                Ad[0] = (mass * Cm[0] - kf * tau.xx) * dx; Ad[1] = (mass * Cm[1] - kf * tau.xy) * dx;
+                Ad[2] = (mass * Cm[2] - kf * tau.xz) * dx; Ad[3] = (mass * Cm[3] - kf * tau.xy) * dx;
+                Ad[4] = (mass * Cm[4] - kf * tau.yy) * dx; Ad[5] = (mass * Cm[5] - kf * tau.yz) * dx;
+                Ad[6] = (mass * Cm[6] - kf * tau.xz) * dx; Ad[7] = (mass * Cm[7] - kf * tau.yz) * dx;
+                Ad[8] = (mass * Cm[8] - kf * tau.zz) * dx;
+                const float P0 = mass * v[0], P1 = mass * v[1], P2 = mass * v[2];
+                // tile-local continuous node coordinate of the new position
+                const float X0 = x[0] * inv_dx - (float)(ox - 1), X1 = x[1] * inv_dx - (float)(oy - 1),
+                            X2 = x[2] * inv_dx - (float)(oz - 1);
+                // base cell floor(X - 0.5) in [0, ST-3] keeps the 3^3 stencil in the tile
+                const bool in_tile = in_dom && X0 >= 0.5f && X1 >= 0.5f && X2 >= 0.5f && X0 < (float)ST - 1.5f &&
+                                     X1 < (float)ST - 1.5f && X2 < (float)ST - 1.5f;
+                float pm = mass;
+                if (in_dom && !in_tile) {
+                    // moved out of the tile: straight to the global grid
+                    pm = 0.f;
+                    float f0, f1, f2;
+                    const int g0 = base_cell(x[0], inv_dx, f0), g1 = base_cell(x[1], inv_dx, f1),
+                              g2 = base_cell(x[2], inv_dx, f2);
+                    float w0[3], w1[3], w2[3];
+                    bspline_w(f0, w0);
+                    bspline_w(f1, w1);
+                    bspline_w(f2, w2);
+                    for (int i = 0; i < 3; ++i)
+                        for (int jj = 0; jj < 3; ++jj)
+                            for (int k = 0; k < 3; ++k) {
+                                const float d0 = (float)i - f0, d1 = (float)jj - f1, d2 = (float)k - f2;
+                                const float wt = w0[i] * w1[jj] * w2[k];
+                                const int I = g0 + i, J = g1 + jj, K = g2 + k;
+                                const int sl = page_slot(D, spar, ep_s, inst, I >> 2, J >> 2, K >> 2);
+                                if (sl >= 0)
+                                    red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K),
+                                               wt * (P0 + Ad[0] * d0 + Ad[1] * d1 + Ad[2] * d2),
+                                               wt * (P1 + Ad[3] * d0 + Ad[4] * d1 + Ad[5] * d2),
+                                               wt * (P2 + Ad[6] * d0 + Ad[7] * d1 + Ad[8] * d2), wt * mass);
+                                else
+                                    set_err(D, ERRB_CFL);
+                            }
+                } else if (!in_dom) {
+                    pm = 0.f;
+                }
+                if (SCAT == 1) {
+                    bnd_m += pm;
+                    float am = fmaxf(fabsf(Ad[0]), fmaxf(fabsf(Ad[1]), fabsf(Ad[2])));
+                    am = fmaxf(am, fmaxf(fabsf(Ad[3]), fmaxf(fabsf(Ad[4]), fabsf(Ad[5]))));
+                    am = fmaxf(am, fmaxf(fabsf(Ad[6]), fmaxf(fabsf(Ad[7]), fabsf(Ad[8]))));
+                    const float ap = fmaxf(fabsf(P0), fmaxf(fabsf(P1), fabsf(P2)));
+                    bnd_v += pm > 0.f ? ap + 4.5f * am : 0.f;
+                }
+                sr[0] = make_float4(X0, X1, X2, pm);
+                sr[1] = make_float4(P0, P1, P2, 0.f);
+                sr[2] = make_float4(Ad[0], Ad[1], Ad[2], Ad[3]);
+                sr[3] = make_float4(Ad[4], Ad[5], Ad[6], Ad[7]);
+                sr[4] = make_float4(Ad[8], 0.f, 0.f, 0.f);
+            }
+            if (MODE != MODE_P2G) bin_end(D, ticket, p);
+        }
+
+        if (SCATTER) {
+            if (SCAT == 1) {
+                // per-chunk fixed-point scales from the sums of the per-particle bounds
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    bnd_m += __shfl_xor_sync(0xffffffffu, bnd_m, o);
+                    bnd_v += __shfl_xor_sync(0xffffffffu, bnd_v, o);
+                }
+                if ((tid & 31) == 0) { S.red[tid >> 5] = bnd_m; S.red[(SUB_THREADS / 32) + (tid >> 5)] = bnd_v; }
+            }
+            __syncthreads();
+            if (SCAT == 1 && tid == 0) {
+                float bm = 0.f, bv = 0.f;
+                for (int w = 0; w < T / 32; ++w) { bm += S.red[w]; bv += S.red[(SUB_THREADS / 32) + w]; }
+                S.scale[0] = bm > 0.f ? 1073741824.f / bm : 1.f;     // 2^30 / bound
+                S.scale[1] = bv > 0.f ? 1073741824.f / bv : 1.f;
+            }
+            if (SCAT == 1) __syncthreads();
+            const float sc_m = SCAT == 1 ? S.scale[0] : 1.f, sc_v = SCAT == 1 ? S.scale[1] : 1.f;
+
+            // ---- B. scatter packets -------------------------------------------
+            // lane-transposed mapping: the warp's lanes take packets S/32 apart
+            // (sorted neighbours share a cell and would hit the same nodes)
+            const int span = rounds * (T >> 5);
+            for (int r = 0; r < rounds; ++r) {
+                const int u = r * T + tid;
+                const int j = (u & 31) * span + (u >> 5);
+                if (j >= cnt) continue;
+                const float4 q0 = S.rec[j * REC_F4];
+                if (!(q0.w > 0.f)) continue;
+                const float4 q1 = S.rec[j * REC_F4 + 1], q2 = S.rec[j * REC_F4 + 2], q3 = S.rec[j * REC_F4 + 3],
+                             q4 = S.rec[j * REC_F4 + 4];
+                const float Ad[9] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w, q4.x};
+                const float b0f = floorf(q0.x - 0.5f), b1f = floorf(q0.y - 0.5f), b2f = floorf(q0.z - 0.5f);
+                const float f0 = q0.x - b0f, f1 = q0.y - b1f, f2 = q0.z - b2f;
+                const int t0 = (int)b0f, t1 = (int)b1f, t2 = (int)b2f;
+                float w0[3], w1[3], w2[3];
+                bspline_w(f0, w0);
+                bspline_w(f1, w1);
+                bspline_w(f2, w2);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float d0 = (float)i - f0;
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj) {
+                        const float d1 = (float)jj - f1;
+                        const float wij = w0[i] * w1[jj];
+                        const float a0 = q1.x + Ad[0] * d0 + Ad[1] * d1, a1 = q1.y + Ad[3] * d0 + Ad[4] * d1,
+                                    a2 = q1.z + Ad[6] * d0 + Ad[7] * d1;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float d2 = (float)k - f2;
+                            const float wt = wij * w2[k];
+                            const float m0 = wt * (a0 + Ad[2] * d2), m1 = wt * (a1 + Ad[5] * d2),
+                                        m2 = wt * (a2 + Ad[8] * d2), mm = wt * q0.w;
+                            const int node = ((t0 + i) * ST + (t1 + jj)) * ST + (t2 + k);
+                            if (SCAT == 0) {
+                                atomicAdd(&S.t.f[node], m0);
+                                atomicAdd(&S.t.f[ST3 + node], m1);
+                                atomicAdd(&S.t.f[2 * ST3 + node], m2);
+                                atomicAdd(&S.t.f[3 * ST3 + node], mm);
+                            } else if (SCAT == 1) {
+                                atomicAdd(&S.t.i[node], __float2int_rn(m0 * sc_v));
+                                atomicAdd(&S.t.i[ST3 + node], __float2int_rn(m1 * sc_v));
+                                atomicAdd(&S.t.i[2 * ST3 + node], __float2int_rn(m2 * sc_v));
+                                atomicAdd(&S.t.i[3 * ST3 + node], __float2int_rn(mm * sc_m));
+                            } else {
+                                const int I = ox - 1 + t0 + i, J = oy - 1 + t1 + jj, K = oz - 1 + t2 + k;
+                                const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 +
+                                                        ((K >> 2) - bz + 1)];
+                                if (sl >= 0)
+                                    red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K), m0, m1,
+                                               m2, mm);
+                                else
+                                    set_err(D, ERRB_CAPACITY);
+                            }
+                        }
+                    }
+                }
+            }
+            if (SCAT != 2) {
+                __syncthreads();
+                // flush: one vector reduction per node that received mass
+                const float iv = 1.f / sc_v, im = 1.f / sc_m;
+                for (int t = tid; t < ST3; t += T) {
+                    float mm, a0, a1, a2;
+                    if (SCAT == 0) {
+                        mm = S.t.f[3 * ST3 + t]; a0 = S.t.f[t]; a1 = S.t.f[ST3 + t]; a2 = S.t.f[2 * ST3 + t];
+                    } else {
+                        const int mi = S.t.i[3 * ST3 + t];
+                        mm = (float)mi * im;
+                        if (mi == 0) mm = 0.f;
+                        a0 = (float)S.t.i[t] * iv; a1 = (float)S.t.i[ST3 + t] * iv; a2 = (float)S.t.i[2 * ST3 + t] * iv;
+                    }
+                    if (mm != 0.f) {
+                        const int i = t / (ST * ST), j = (t / ST) % ST, k = t % ST;
+                        const int I = ox - 1 + i, J = oy - 1 + j, K = oz - 1 + k;
+                        const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 + ((K >> 2) - bz + 1)];
+                        if (sl >= 0) red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K), a0, a1, a2, mm);
+                        else set_err(D, ERRB_CAPACITY);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// export: records -> caller layout
+// ---------------------------------------------------------------------------
+__global__ void k_export(Dev D, float *x, float *v, float *C, float *F) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < D.n; p += gridDim.x * blockDim.x) {
+        const float4 *r = D.rec + (size_t)p * REC_F4;
+        float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6];
+        if (x) { x[3 * p] = r0.x; x[3 * p + 1] = r0.y; x[3 * p + 2] = r0.z; }
+        if (v) { v[3 * p] = r1.x; v[3 * p + 1] = r1.y; v[3 * p + 2] = r1.z; }
+        if (C) {
+            float c[9] = {r2.x, r2.y, r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x};
+            for (int i = 0; i < 9; ++i) C[9 * p + i] = c[i];
+        }
+        if (F) {
+            float f[9] = {r4.y, r4.z, r4.w, r5.x, r5.y, r5.z, r5.w, r6.x, r6.y};
+            for (int i = 0; i < 9; ++i) F[9 * p + i] = f[i];
+        }
+    }
+}
+
+// dense copy of one grid buffer (debug / parity): m and mv per node of every
+// active block, written into caller arrays of R0*R1*R2 (*3) per instance
+__global__ void k_grid_dense(Dev D, int par, int which, float *m_out, float *mv_out) {
+    const unsigned total = min(D.ctr[CTR_N_ACTIVE + par], D.max_active) * BLK_NODES;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        unsigned slot = i >> 6, l = i & 63u;
+        int inst, bx, by, bz;
+        key_coords(D, D.active[par][slot], inst, bx, by, bz);
+        int I = bx * BLK + (int)(l >> 4), J = by * BLK + (int)((l >> 2) & 3u), K = bz * BLK + (int)(l & 3u);
+        size_t nd = (size_t)inst * D.R[0] * D.R[1] * D.R[2] + ((size_t)I * D.R[1] + J) * D.R[2] + K;
+        float4 a = which ? D.gv[par][i] : D.gmv[par][i];
+        m_out[nd] = a.w;
+        mv_out[3 * nd] = a.x;
+        mv_out[3 * nd + 1] = a.y;
+        mv_out[3 * nd + 2] = a.z;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st) {
+    k_load<<<grid_for(D.n, 256), 256, 0, st>>>(D, a.x, a.v, a.C, a.F, a.vol, a.mat, a.inst, a.params, a.table);
+}
+void launch_bin(const Dev &D, cudaStream_t st) { k_bin<<<grid_for(D.n, 256), 256, 0, st>>>(D); }
+void launch_plan(const Dev &D, int bump_par, cudaStream_t st) { k_plan<<<1, 1024, 0, st>>>(D, bump_par); }
+void launch_activate_sort(const Dev &D, int par, int do_sort, int grid, cudaStream_t st) {
+    k_activate_sort<<<grid, 256, 0, st>>>(D, par, do_sort);
+}
+void launch_grid_update(const Dev &D, int par, int bump_par, int grid, cudaStream_t st, int keep_momentum) {
+    k_grid_update<<<grid, 256, 0, st>>>(D, par, bump_par, keep_momentum);
+}
+template <int MODE, int SCAT> static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
+    k_substep<MODE, SCAT><<<grid, SUB_THREADS, sizeof(SubstepSmem), st>>>(D, gpar, spar);
+}
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st) {
+    (void)threads;
+    if (mode == MODE_G2P) { launch_sub<MODE_G2P, 2>(D, gpar, spar, grid, st); return; }
+    if (mode == MODE_P2G) {
+        if (D.scatter == 0) launch_sub<MODE_P2G, 0>(D, gpar, spar, grid, st);
+        else if (D.scatter == 1) launch_sub<MODE_P2G, 1>(D, gpar, spar, grid, st);
+        else launch_sub<MODE_P2G, 2>(D, gpar, spar, grid, st);
+        return;
+    }
+    if (D.scatter == 0) launch_sub<MODE_FUSED, 0>(D, gpar, spar, grid, st);
+    else if (D.scatter == 1) launch_sub<MODE_FUSED, 1>(D, gpar, spar, grid, st);
+    else launch_sub<MODE_FUSED, 2>(D, gpar, spar, grid, st);
+}
+void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st) {
+    k_export<<<grid_for(D.n, 256), 256, 0, st>>>(D, x, v, C, F);
+}
+void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st) {
+    k_grid_dense<<<1024, 256, 0, st>>>(D, par, which, m, mv);
+}
+template <int MODE, int SCAT> static int occ_of() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_substep<MODE, SCAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SubstepSmem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT>, SUB_THREADS, sizeof(SubstepSmem));
+    return nb;
+}
+int substep_occupancy(int mode, int scatter, int threads) {
+    (void)threads;
+    if (mode == MODE_G2P) return occ_of<MODE_G2P, 2>();
+    if (mode == MODE_P2G) return scatter == 0 ? occ_of<MODE_P2G, 0>() : scatter == 1 ? occ_of<MODE_P2G, 1>() : occ_of<MODE_P2G, 2>();
+    return scatter == 0 ? occ_of<MODE_FUSED, 0>() : scatter == 1 ? occ_of<MODE_FUSED, 1>() : occ_of<MODE_FUSED, 2>();
+}
+int substep_chunk_max() { return CH_MAX; }
+
+}  // namespace mpm

@@ -1,0 +1,95 @@
+// mpm_internal.h -- declarations shared by the host side (mpm_api.cu) and the
+// kernel translation units of libmpm.  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mpm.h"
+#include "mpm_dev.cuh"
+
+namespace mpm {
+
+// material table as device arrays
+struct MatTable {
+    int n;
+    const float *E, *nu, *rho, *yield, *alpha;
+    const int *elastic, *plastic;
+};
+
+struct LoadArgs {
+    const float *x, *v, *C, *F, *vol, *params;
+    const int *mat, *inst;
+    MatTable table;
+};
+
+inline int grid_for(long long n, int threads, int cap = 152 * 16) {
+    long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st);
+void launch_bin(const Dev &D, cudaStream_t st);
+void launch_plan(const Dev &D, int par_next, cudaStream_t st);
+void launch_activate_sort(const Dev &D, int par, int do_sort, int grid, cudaStream_t st);
+void launch_grid_update(const Dev &D, int par, int bump_par, int grid, cudaStream_t st, int keep_momentum = 0);
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st);
+void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st);
+void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
+int substep_occupancy(int mode, int scatter, int threads);
+int substep_chunk_max();
+
+// recorded trajectory and reverse-pass buffers
+struct AdjointStore {
+    std::vector<float4 *> ckpt;     // ckpt[c]: records at recorded substep c * ckpt_every
+    float4 *tape = nullptr;         // ckpt_every states of one segment
+    size_t tape_states = 0;
+    float4 *adj[2] = {nullptr, nullptr};   // adjoint state (x v C F) per particle, 6 float4
+    float4 *gpar = nullptr;         // parameter gradients per particle (log E, nu, yield, 0)
+    float4 *gbar = nullptr;         // grid adjoint pool
+    float *frames = nullptr;        // staged dL/dx
+    size_t frames_bytes = 0;
+    long long cap = 0;
+    unsigned pool = 0;
+};
+void free_adjoint(AdjointStore &a);
+
+}  // namespace mpm
+
+struct mpm_ctx {
+    int device = 0;
+    int sm_count = 0;
+    int R[3];
+    float dx, dt, g[3];
+    mpm_options opt;
+    std::vector<mpm_material> table;
+    mpm::Dev D;
+    float *mE = nullptr, *mnu = nullptr, *mrho = nullptr, *myield = nullptr, *malpha = nullptr;
+    int *mel = nullptr, *mpl = nullptr;
+    long long cap = 0;            // particle capacity
+    long long total_blocks = 0;
+    unsigned pool_blocks = 0;     // allocated grid pool capacity (blocks)
+    unsigned chunk_cap = 0;
+    void *stage = nullptr;        // staging for host inputs / outputs
+    size_t stage_bytes = 0;
+    bool loaded = false;
+    mpm_status sticky = MPM_OK;
+    std::string msg;
+    int threads = 256;
+    int grid_sub[3] = {0, 0, 0};
+    int grid_small = 0;
+    long long recorded = 0;       // substeps recorded since the last load / reset
+    bool record_broken = false;
+    mpm::AdjointStore adj;
+};
+
+namespace mpm {
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
+mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
+mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);
+mpm_status ctx_check(mpm_ctx *ctx, cudaStream_t st);
+bool is_device_ptr(const void *p);
+}  // namespace mpm

@@ -1,0 +1,130 @@
+"""Python front end of libmpm: a Simulator that owns one mpm_ctx, and the
+torch.autograd.Function that differentiates a trajectory loss through the
+library's hand-written adjoint.  PyTorch supplies device memory and streams
+only; every step of the simulation runs in libmpm's kernels."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _stream(s=None):
+    s = s if s is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(a, dtype, device, width=None):
+    if a is None:
+        return None
+    t = torch.as_tensor(a, dtype=dtype)
+    if width is not None:
+        t = t.reshape(-1, width)
+    return t.to(device).contiguous()
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Simulator:
+    """One simulation context (one or more independent grids)."""
+
+    def __init__(self, grid_res, dx, dt, gravity, materials, n_instances=1, walls=None, bound=3, ckpt_every=20,
+                 chunk=0, threads=0, max_active_blocks=0, max_particles=0, scatter=1, device="cuda"):
+        if np.isscalar(grid_res):
+            grid_res = (grid_res,) * 3
+        self.grid_res = tuple(int(r) for r in grid_res)
+        self.dx, self.dt = float(dx), float(dt)
+        self.device = torch.device(device)
+        opt = L.mpm_default_options()
+        opt.n_instances = int(n_instances)
+        opt.bound = int(bound)
+        if walls is not None:
+            for i, w in enumerate(walls):
+                opt.walls[i] = int(w)
+        opt.ckpt_every = int(ckpt_every)
+        opt.chunk = int(chunk)
+        opt.threads = int(threads)
+        opt.scatter = int(scatter)
+        opt.max_active_blocks = int(max_active_blocks)
+        opt.max_particles = int(max_particles)
+        self.n_instances = int(n_instances)
+        self.materials = list(materials)
+        with torch.cuda.device(self.device):
+            self.ctx = L.mpm_create(self.grid_res, self.dx, self.dt, gravity, self.materials, opt)
+        self.n = 0
+
+    @classmethod
+    def from_scene(cls, sc, **kw):
+        kw.setdefault("n_instances", sc.n_instances)
+        kw.setdefault("ckpt_every", sc.ckpt_every or 20)
+        return cls(sc.grid_res, sc.dx, sc.dt, sc.gravity, sc.materials, **kw)
+
+    def load_scene(self, sc, params=None, stream=None):
+        return self.load(sc.x, sc.vol, sc.mat_id, v=sc.v, instance=sc.instance,
+                         params=sc.params if params is None else params, stream=stream)
+
+    def load(self, x, vol, material_id, v=None, C=None, F=None, instance=None, params=None, stream=None):
+        dv = self.device
+        x = _dev(x, torch.float32, dv, 3)
+        n = x.shape[0]
+        args = [x, _dev(v, torch.float32, dv, 3), _dev(C, torch.float32, dv, 9), _dev(F, torch.float32, dv, 9),
+                _dev(vol, torch.float32, dv), _dev(material_id, torch.int32, dv), _dev(instance, torch.int32, dv),
+                _dev(params, torch.float32, dv, 3)]
+        L.mpm_load_particles(self.ctx, n, *[_p(a) for a in args], _stream(stream))
+        self.n = n
+        return self
+
+    def step(self, n_substeps, record=False, stream=None):
+        L.mpm_step(self.ctx, int(n_substeps), int(bool(record)), _stream(stream))
+
+    def get(self, stream=None):
+        n = self.n
+        out = {"x": torch.empty((n, 3), device=self.device), "v": torch.empty((n, 3), device=self.device),
+               "C": torch.empty((n, 3, 3), device=self.device), "F": torch.empty((n, 3, 3), device=self.device)}
+        L.mpm_get_particles(self.ctx, _p(out["x"]), _p(out["v"]), _p(out["C"]), _p(out["F"]), _stream(stream))
+        return out
+
+    def positions(self, out=None, stream=None):
+        out = torch.empty((self.n, 3), device=self.device) if out is None else out
+        L.mpm_get_particles(self.ctx, _p(out), None, None, None, _stream(stream))
+        return out
+
+    def sync(self, stream=None):
+        L.mpm_sync(self.ctx, _stream(stream))
+
+    def stats(self, stream=None):
+        return L.mpm_stats(self.ctx, _stream(stream))
+
+    def record_reset(self):
+        L.mpm_record_reset(self.ctx)
+
+    def backward(self, frame_sub, dL_dx, want_state0=False, stream=None):
+        dL_dx = _dev(dL_dx, torch.float32, self.device).reshape(len(frame_sub), self.n, 3).contiguous()
+        g = torch.empty((self.n, 3), device=self.device)
+        a0 = torch.empty((self.n, 24), device=self.device) if want_state0 else None
+        L.mpm_backward(self.ctx, list(frame_sub), _p(dL_dx), _p(g), _p(a0), _stream(stream))
+        return (g, a0) if want_state0 else g
+
+    def debug_p2g(self, stream=None):
+        nn = self.n_instances * self.grid_res[0] * self.grid_res[1] * self.grid_res[2]
+        m = torch.empty(nn, device=self.device)
+        mv = torch.empty(nn * 3, device=self.device)
+        L.mpm_debug_p2g(self.ctx, _p(m), _p(mv), _stream(stream))
+        shape = (self.n_instances,) + self.grid_res
+        return m.reshape(shape), mv.reshape(shape + (3,))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            L.mpm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

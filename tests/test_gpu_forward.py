@@ -1,0 +1,219 @@
+"""GPU forward parity: libmpm (FP32, through the C ABI) against the FP64 oracle
+on the same seeded inputs.
+
+Tolerances: grid mass and momentum within 1e-5 relative per teacher-forced
+substep, with the norm ||diff||_inf / max(||ref||_inf, ||m_ref||_inf |g| dt);
+positions within 1e-4 dx after 100 free-running substeps (elastic cases)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_01723_gb300 import scenes  # noqa: E402
+
+GRID_TOL = 1e-5
+POS_TOL_DX = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sim_mod():
+    from __graft_entry__ import build
+    build()
+    from paper_2602_01723_gb300 import sim
+    return sim
+
+
+def to_np(state):
+    return {k: v.detach().double().cpu().numpy() for k, v in state.items()}
+
+
+def oracle_setup(orc, sc, n_instances=1):
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
+    return cfg, mat
+
+
+def grid_rel(gpu, ref, mref, g, dt):
+    floor = np.abs(mref).max() * np.linalg.norm(g) * dt
+    return np.abs(gpu - ref).max() / max(np.abs(ref).max(), floor, 1e-300)
+
+
+def stressed_state(sc, seed=5, vs=0.5, cs=5.0, fs=0.02):
+    """The scene's particles with a random velocity, affine field and a
+    deformation gradient away from I (incl. a rotation)."""
+    rng = np.random.default_rng(seed)
+    n = sc.n
+    v = sc.v + vs * rng.standard_normal((n, 3))
+    C = cs * rng.standard_normal((n, 3, 3))
+    th = 0.3
+    Rz = np.array([[np.cos(th), -np.sin(th), 0], [np.sin(th), np.cos(th), 0], [0, 0, 1]])
+    F = np.array([Rz @ (np.eye(3) + fs * rng.standard_normal((3, 3))) for _ in range(n)])
+    return v.astype(np.float32), C.astype(np.float32), F.astype(np.float32)
+
+
+def teacher_forced_p2g(orc, sim_mod, sc, v, C, F):
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F, instance=sc.instance, params=sc.params)
+    m, mv = s.debug_p2g()
+    st = to_np(s.get())
+    cfg, mat = oracle_setup(orc, sc)
+    gm, gmv = orc.p2g(cfg, orc.new_state(st["x"], st["v"], st["C"], st["F"]), mat)
+    m = m[0].double().cpu().numpy()
+    mv = mv[0].double().cpu().numpy()
+    s.close()
+    return grid_rel(m, gm, gm, sc.gravity, sc.dt), grid_rel(mv, gmv, gm, sc.gravity, sc.dt)
+
+
+@pytest.mark.parametrize("name", ["cube_8k", "ball_512"])
+def test_p2g_grid_teacher_forced(orc, sim_mod, name):
+    sc = scenes.WORKLOADS[name]()
+    em, emv = teacher_forced_p2g(orc, sim_mod, sc, *stressed_state(sc))
+    assert em < GRID_TOL and emv < GRID_TOL, (em, emv)
+
+
+def test_p2g_grid_teacher_forced_plastic_and_neo_hookean(orc, sim_mod):
+    sc = scenes.cube_8k()
+    sc.materials = [scenes.material(1, 0, 2e4, 0.3, 10.0), scenes.material(0, 1, 1e4, 0.3, 10.0, yield_stress=50.0),
+                    scenes.material(0, 2, 1e4, 0.25, 10.0)]
+    sc.mat_id = (np.arange(sc.n) % 3).astype(np.int32)
+    em, emv = teacher_forced_p2g(orc, sim_mod, sc, *stressed_state(sc, fs=0.1))
+    assert em < GRID_TOL and emv < GRID_TOL, (em, emv)
+
+
+def substep_compare(orc, sim_mod, sc, v, C, F, n_sub=1):
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F, instance=sc.instance, params=sc.params)
+    st0 = to_np(s.get())
+    s.step(n_sub)
+    s.sync()
+    st1 = to_np(s.get())
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(st0["x"], st0["v"], st0["C"], st0["F"]), mat, n_sub)
+    s.close()
+    return st1, ref
+
+
+def test_one_substep_teacher_forced_all_models(orc, sim_mod):
+    sc = scenes.cube_8k()
+    sc.materials = [scenes.material(0, 0, 1e4, 0.3, 10.0), scenes.material(1, 0, 2e4, 0.3, 10.0),
+                    scenes.material(0, 1, 1e4, 0.3, 10.0, yield_stress=50.0), scenes.material(0, 2, 1e4, 0.25, 10.0)]
+    sc.mat_id = (np.arange(sc.n) % 4).astype(np.int32)
+    v, C, F = stressed_state(sc, fs=0.1)
+    got, ref = substep_compare(orc, sim_mod, sc, v, C, F)
+    vs = np.abs(ref["v"]).max()
+    assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * vs
+    assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
+    assert np.abs(got["C"] - ref["C"]).max() < 1e-5 * np.abs(ref["C"]).max()
+    # F after the return map: compare per particle relative to |F|
+    assert np.abs(got["F"] - ref["F"]).max() < 2e-5
+
+
+def test_cube_8k_positions_after_100_substeps(orc, sim_mod):
+    """The 8,192-particle cube, 100 free-running substeps: positions within
+    1e-4 dx of the FP64 oracle."""
+    sc = scenes.cube_8k()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(sc.n_substeps)
+    s.sync()
+    got = to_np(s.get())
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, sc.n_substeps)
+    err = np.abs(got["x"] - ref["x"]).max() / sc.dx
+    assert err < POS_TOL_DX, err
+
+
+def test_ball_512_free_running_with_floor_contact(orc, sim_mod):
+    sc = scenes.ball_512()
+    sc.params = None     # table values: E 5e3, nu 0.3
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(200)
+    s.sync()
+    got = to_np(s.get())
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, 200)
+    err = np.abs(got["x"] - ref["x"]).max() / sc.dx
+    assert err < POS_TOL_DX, err
+
+
+def test_chunks_span_several_per_block_and_ragged_tail(orc, sim_mod):
+    """Thousands of particles in one 4^3 block: several work chunks per block
+    with a ragged last chunk, and a second block with a single particle."""
+    rng = np.random.default_rng(3)
+    x = 0.5 + rng.uniform(0.0, 4.0 / 32 - 1e-4, (3001, 3)).astype(np.float32) - 0.5 / 32
+    x[-1] = [0.25, 0.25, 0.25]
+    n = len(x)
+    sc = scenes.Scene("dense_block", 32, 1e-4, 5, x, np.zeros((n, 3), np.float32),
+                      np.full(n, (0.5 / 32) ** 3 / 8, np.float32), np.zeros(n, np.int32),
+                      [scenes.material(0, 0, 1e3, 0.3, 1.0)])
+    v, C, F = stressed_state(sc, vs=0.1, cs=1.0, fs=0.01)
+    got, ref = substep_compare(orc, sim_mod, sc, v, C, F, n_sub=5)
+    assert np.abs(got["x"] - ref["x"]).max() < 1e-5 * sc.dx
+    assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * np.abs(ref["v"]).max()
+
+
+def test_out_of_domain_reports_error(sim_mod):
+    from paper_2602_01723_gb300 import _lib as L
+    sc = scenes.cube_8k()
+    x = sc.x.copy()
+    x[7] = [0.005, 0.5, 0.5]
+    s = sim_mod.Simulator.from_scene(sc)
+    with pytest.raises(L.MpmError) as e:
+        s.load(x, sc.vol, sc.mat_id)
+    assert e.value.status == 4
+    with pytest.raises(L.MpmError):
+        s.step(1)
+    s.load_scene(sc)        # a valid load clears the error state
+    s.step(2)
+    s.sync()
+    s.close()
+
+
+def test_leaving_the_domain_mid_run_reports_error(sim_mod):
+    from paper_2602_01723_gb300 import _lib as L
+    sc = scenes.cube_8k()
+    v = np.tile([0.0, 0.0, 40.0], (sc.n, 1)).astype(np.float32)    # leaves z+ within ~100 substeps
+    s = sim_mod.Simulator(sc.grid_res, sc.dx, sc.dt, (0, 0, 0), sc.materials, walls=(0,) * 6)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v)
+    s.step(200)
+    with pytest.raises(L.MpmError) as e:
+        s.sync()
+    assert e.value.status in (4, 9)
+    s.close()
+
+
+def test_three_objects_full_size_teacher_forced(orc, sim_mod):
+    """The 300k-particle, 128^3 three-object scene at full size, in the
+    launch configuration bench.py times: after 1,400 substeps (the objects
+    have reached the floor) one teacher-forced P2G grid against the oracle,
+    and one teacher-forced substep on a sample of particles."""
+    sc = scenes.three_objects_300k()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(1400)
+    s.sync()
+    st = s.get()
+    m, mv = s.debug_p2g()
+    stn = to_np(st)
+    cfg, mat = oracle_setup(orc, sc)
+    gm, gmv = orc.p2g(cfg, orc.new_state(stn["x"], stn["v"], stn["C"], stn["F"]), mat)
+    em = grid_rel(m[0].double().cpu().numpy(), gm, gm, sc.gravity, sc.dt)
+    emv = grid_rel(mv[0].double().cpu().numpy(), gmv, gm, sc.gravity, sc.dt)
+    assert em < GRID_TOL and emv < GRID_TOL, (em, emv)
+    # one substep: every particle on the GPU, the oracle's G2P sampled
+    s.step(1)
+    s.sync()
+    got = to_np(s.get())
+    gv = orc.grid_update(cfg, gm, gmv)
+    idx = np.random.default_rng(0).choice(sc.n, 4000, replace=False)
+    sub = orc.new_state(stn["x"][idx], stn["v"][idx], stn["C"][idx], stn["F"][idx])
+    ref = orc.g2p(cfg, sub, mat.subset(idx), gv)
+    assert np.abs(got["x"][idx] - ref["x"]).max() < 1e-4 * sc.dx
+    assert np.abs(got["v"][idx] - ref["v"]).max() < 1e-4 * np.abs(ref["v"]).max()
+    st_ = s.stats()
+    assert st_["device_error"] == 0
+    s.close()
