@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the MLS-MPM substep (libmpm) on one node.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (the configuration the headline metric is quoted on): the
+300,000-particle three-object scene (sphere elastic, torus plasticine, box
+sand) on a 128^3 grid, dt 5e-5, synthetic seeded inputs.  One step = one full
+2,000-substep forward simulation from the initial state, which is resident in
+HBM when the timed region starts; L2 is flushed (a 256 MiB write) between
+timed steps, outside the timed events.  With N > 1 (torchrun, one process per
+GPU, NCCL) every rank runs its own replica (weak scaling; the single scene is
+not sharded), and rank 0 prints one JSON line with the max-over-ranks time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-substeps/sec fwd and fwd+bwd at 1 GB300; HBM roofline %; err vs FP64"
+UNIT = "particle-substeps/s"
+WORKLOAD = "three_objects_300k"
+# algorithmic bytes per particle-substep of the forward substep: the particle
+# state read once and written once (2 x 96 B), the material word (4 B) and the
+# grid (about 6 B per particle: 16 B written and read per active node, ~0.19
+# active nodes per particle)
+FWD_BYTES_PER_PS = 200.0
+ORACLE_SAMPLE_SUBSTEPS = 30
+REF_STEP_SUBSTEPS = 4
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i in range(4) if r[i].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    if n_gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", 0))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist, dist.get_rank(), dist.get_world_size(), local
+    torch.cuda.set_device(0)
+    return None, 0, 1, 0
+
+
+def oracle_rate(sc, n_sub):
+    """Timed FP64 oracle on the first n_sub substeps of the workload."""
+    import oracle as orc
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
+    st = orc.new_state(sc.x, sc.v)
+    t0 = time.perf_counter()
+    orc.run(cfg, st, mat, n_sub)
+    t = time.perf_counter() - t0
+    return sc.n * n_sub / t, t
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle timed on the host cores."""
+    if "RANK" in os.environ and int(os.environ["RANK"]) != 0:
+        return
+    from paper_2602_01723_gb300 import scenes
+    import oracle as orc
+    orc.build()
+    sc = scenes.WORKLOADS[WORKLOAD]()
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
+    st = orc.new_state(sc.x, sc.v)
+    for _ in range(args.warmup):
+        st = orc.run(cfg, st, mat, REF_STEP_SUBSTEPS)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = orc.run(cfg, st, mat, REF_STEP_SUBSTEPS)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = sc.n * REF_STEP_SUBSTEPS * args.steps / tot
+    sample = "%d substeps of the %d-particle scene per step, FP64, 1 thread" % (REF_STEP_SUBSTEPS, sc.n)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "particles": sc.n, "grid": sc.grid_res,
+                                            "dt": sc.dt, "substeps_per_step": REF_STEP_SUBSTEPS},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    dist, rank, world, local = dist_setup(args.gpus)
+    from __graft_entry__ import build
+    if rank == 0 or dist is None:
+        build()
+    if dist is not None:
+        dist.barrier()
+        build()
+    from paper_2602_01723_gb300 import scenes
+    from paper_2602_01723_gb300.sim import Simulator, _p, _stream
+    from paper_2602_01723_gb300 import _lib as L
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sc = scenes.WORKLOADS[WORKLOAD]()
+    n, S = sc.n, sc.n_substeps
+    sim = Simulator.from_scene(sc)
+    # initial state resident on the device
+    x0 = torch.as_tensor(sc.x, device=dev).contiguous()
+    v0 = torch.as_tensor(sc.v, device=dev).contiguous()
+    vol = torch.as_tensor(sc.vol, device=dev).contiguous()
+    mid = torch.as_tensor(sc.mat_id, dtype=torch.int32, device=dev).contiguous()
+    flush = torch.empty(256 * 2 ** 20 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    sim.n = n
+
+    def one_step():
+        L.mpm_load_particles(sim.ctx, n, _p(x0), _p(v0), None, None, _p(vol), _p(mid), None, None, _stream())
+        sim.step(S)
+
+    for _ in range(args.warmup):
+        one_step()
+    sim.sync()
+    torch.cuda.synchronize()
+
+    l0 = sim.stats()["launches"]
+    sim.trace(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))                 # L2 flush between timed steps, outside the events
+            ev[k][0].record(stream)
+            one_step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    sim.sync()
+    tr = sim.trace(False)
+    launches = sim.stats()["launches"] - l0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * n * S * args.steps / (tot_ms * 1e-3)
+
+    # roofline of the dominant kernel: the fused G2P + update + P2G kernel
+    fused_ms, fused_n = tr["fused"]
+    peak, peak_kind = load_peaks()
+    avg_fused_s = fused_ms * 1e-3 / max(fused_n, 1)
+    achieved = FWD_BYTES_PER_PS * n / avg_fused_s / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("k_substep_fused_three_objects_300k_bytes_per_launch")
+
+    # end to end through the C ABI with host (pinned) buffers
+    xh = torch.as_tensor(sc.x).pin_memory()
+    vh = torch.as_tensor(sc.v).pin_memory()
+    volh = torch.as_tensor(sc.vol).pin_memory()
+    midh = torch.as_tensor(sc.mat_id, dtype=torch.int32).pin_memory()
+    xout = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.mpm_load_particles(sim.ctx, n, _p(xh), _p(vh), None, None, _p(volh), _p(midh), None, None, _stream())
+        sim.step(S)
+        L.mpm_get_particles(sim.ctx, _p(xout), None, None, None, _stream())
+        sim.sync()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_v = world * n * S / (statistics.mean(e2e_ms) * 1e-3)
+    h2d = n * (12 + 12 + 4 + 4)
+    d2h = n * 12
+
+    # error against the FP64 oracle: one teacher-forced substep from the GPU
+    # state after the full run (grid momentum over all nodes, positions on a
+    # 4,000-particle sample)
+    err = {}
+    if rank == 0:
+        import oracle as orc
+        st = {k: v.double().cpu().numpy() for k, v in sim.get().items()}
+        m, mv = sim.debug_p2g()
+        cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+        mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
+        ost = orc.new_state(st["x"], st["v"], st["C"], st["F"])
+        gm, gmv = orc.p2g(cfg, ost, mat)
+        floor = np.abs(gm).max() * 9.8 * sc.dt
+        err["grid_m_rel"] = float(np.abs(m[0].double().cpu().numpy() - gm).max() / max(np.abs(gm).max(), floor))
+        err["grid_mv_rel"] = float(np.abs(mv[0].double().cpu().numpy() - gmv).max() / max(np.abs(gmv).max(), floor))
+        sim.step(1)
+        got = sim.get()["x"].double().cpu().numpy()
+        gv = orc.grid_update(cfg, gm, gmv)
+        idx = np.random.default_rng(0).choice(n, 4000, replace=False)
+        sub = orc.new_state(st["x"][idx], st["v"][idx], st["C"][idx], st["F"][idx])
+        ref = orc.g2p(cfg, sub, mat.subset(idx), gv)
+        err["x_one_substep_max_dx"] = float(np.abs(got[idx] - ref["x"]).max() / sc.dx)
+        err["note"] = "teacher-forced: FP32 GPU vs FP64 oracle from the same state after %d substeps" % S
+
+    if rank == 0:
+        cpu_v, cpu_t = oracle_rate(sc, ORACLE_SAMPLE_SUBSTEPS)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded shell + interior scene; the paper's 3DGS scenes are not available)",
+            "config": {"workload": WORKLOAD, "particles": n, "grid": sc.grid_res, "dt": sc.dt,
+                       "substeps_per_step": S, "materials": "elastic FCR / von Mises / Drucker-Prager",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": "replicas" if world > 1 else "1 GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_substep<fused>", "avg_launch_us": avg_fused_s * 1e6,
+                         "launches": fused_n, "bytes_per_particle_substep": FWD_BYTES_PER_PS,
+                         "peak_kind": peak_kind},
+            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d substeps of the %d-particle scene, FP64 oracle, 1 thread, %.1f s"
+                                       % (ORACLE_SAMPLE_SUBSTEPS, n, cpu_t)},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "err_vs_fp64": err,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

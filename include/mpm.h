@@ -148,8 +148,18 @@ MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream);
 /* Diagnostics copied to host (synchronises): counters[0] particles,
  * [1] occupied blocks, [2] active blocks of the last grid, [3] work chunks,
  * [4] FP64 SVD fallbacks so far, [5] substeps recorded, [6] device error
- * word, [7] grid pool capacity (blocks). */
-MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[8], void *stream);
+ * word, [7] grid pool capacity (blocks), [8] kernels launched by this
+ * context so far; [9..15] zero. */
+MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream);
+
+/* Tracing of the substep kernel.  When ms and count are not NULL, first
+ * returns the summed device time (CUDA events recorded on the launching
+ * stream around each launch) and the number of traced launches since the last
+ * call, for the three variants: [0] first-substep scatter, [1] fused
+ * gather + update + scatter, [2] last-substep gather; this waits for the
+ * recorded events.  Then switches tracing on (enable != 0) or off and clears
+ * the record. */
+MPM_API mpm_status mpm_trace(mpm_ctx *ctx, int32_t enable, double ms[3], int64_t count[3]);
 
 /* Diagnostic: P2G of the current state into dense device arrays m
  * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at

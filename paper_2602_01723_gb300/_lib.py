@@ -55,6 +55,7 @@ SIGNATURES = {
     "mpm_last_error": (ctypes.c_char_p, [_ctx_p]),
     "mpm_destroy": (ctypes.c_int, [_ctx_p]),
     "mpm_debug_p2g": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+    "mpm_trace": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _i64p]),
 }
 
 _lib = None
@@ -132,11 +133,20 @@ def mpm_sync(ctx, stream):
 
 
 def mpm_stats(ctx, stream):
-    c = (ctypes.c_int64 * 8)()
+    c = (ctypes.c_int64 * 16)()
     check(lib().mpm_stats(ctx, c, stream), ctx)
     keys = ["particles", "occupied_blocks", "active_blocks", "chunks", "fp64_svd_fallbacks", "recorded",
-            "device_error", "pool_blocks"]
+            "device_error", "pool_blocks", "launches"]
     return dict(zip(keys, list(c)))
+
+
+def mpm_trace(ctx, enable):
+    """Returns {variant: (ms, launches)} recorded since the last call, then
+    switches tracing on or off."""
+    ms = (ctypes.c_double * 3)()
+    cnt = (ctypes.c_int64 * 3)()
+    check(lib().mpm_trace(ctx, int(enable), ms, cnt), ctx)
+    return {"p2g": (ms[0], cnt[0]), "fused": (ms[1], cnt[1]), "g2p": (ms[2], cnt[2])}
 
 
 def mpm_last_error(ctx):

@@ -169,25 +169,55 @@ cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 // ===========================================================================
 namespace mpm {
 
+void L_plan(mpm_ctx *ctx, int bump_par, cudaStream_t st) { launch_plan(ctx->D, bump_par, st); ++ctx->launches; }
+void L_activate_sort(mpm_ctx *ctx, int par, int do_sort, cudaStream_t st) {
+    launch_activate_sort(ctx->D, par, do_sort, ctx->grid_small, st);
+    ++ctx->launches;
+}
+void L_grid_update(mpm_ctx *ctx, int par, int bump_par, cudaStream_t st, int keep_momentum) {
+    launch_grid_update(ctx->D, par, bump_par, ctx->grid_small, st, keep_momentum);
+    ++ctx->launches;
+}
+void L_bin(mpm_ctx *ctx, cudaStream_t st) { launch_bin(ctx->D, st); ++ctx->launches; }
+void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
+    cudaEvent_t *ev = nullptr;
+    if (ctx->trace_on) {
+        std::vector<cudaEvent_t> &pool = ctx->trace_ev[mode];
+        size_t u = ctx->trace_used[mode];
+        while (pool.size() < u + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); break; }
+            pool.push_back(e);
+        }
+        if (pool.size() >= u + 2) {
+            ev = &pool[u];
+            ctx->trace_used[mode] = u + 2;
+            cudaEventRecord(ev[0], st);
+        }
+    }
+    launch_substep(ctx->D, mode, gpar, spar, ctx->grid_sub[mode], ctx->threads, st);
+    ++ctx->launches;
+    if (ev) cudaEventRecord(ev[1], st);
+}
+
 // forward of n substeps from the current state (bins must be valid);
 // leaves the state advanced and binned
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
-    Dev &D = ctx->D;
     if (n_sub <= 0) return MPM_OK;
-    launch_plan(D, 0, st);
-    launch_activate_sort(D, 0, 1, ctx->grid_small, st);
-    launch_substep(D, 0, 0, 0, ctx->grid_sub[0], ctx->threads, st);
+    L_plan(ctx, 0, st);
+    L_activate_sort(ctx, 0, 1, st);
+    L_substep(ctx, 0, 0, 0, st);
     for (int s = 0; s < n_sub; ++s) {
         int par = s & 1;
         bool last = s == n_sub - 1;
-        launch_grid_update(D, par, last ? -1 : (par ^ 1), ctx->grid_small, st);
+        L_grid_update(ctx, par, last ? -1 : (par ^ 1), st);
         if (!last) {
-            launch_activate_sort(D, par ^ 1, 1, ctx->grid_small, st);
-            launch_substep(D, 1, par, par ^ 1, ctx->grid_sub[1], ctx->threads, st);
-            launch_plan(D, -1, st);
+            L_activate_sort(ctx, par ^ 1, 1, st);
+            L_substep(ctx, 1, par, par ^ 1, st);
+            L_plan(ctx, -1, st);
         } else {
-            if (s > 0) launch_activate_sort(D, -1, 1, ctx->grid_small, st);   // sort for the latest plan
-            launch_substep(D, 2, par, 0, ctx->grid_sub[2], ctx->threads, st);
+            if (s > 0) L_activate_sort(ctx, -1, 1, st);   // sort for the latest plan
+            L_substep(ctx, 2, par, 0, st);
         }
     }
     cudaError_t e = cudaGetLastError();
@@ -367,7 +397,8 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     CK(cudaMemsetAsync(D.bcount, 0, (size_t)ctx->total_blocks * sizeof(unsigned), st));
     CK(cudaMemsetAsync(D.ctr + CTR_N_OCC, 0, sizeof(unsigned), st));
     launch_load(D, a, st);
-    launch_bin(D, st);
+    ++ctx->launches;
+    L_bin(ctx, st);
     CKLAUNCH();
     ctx->sticky = MPM_OK;
     ctx->loaded = true;
@@ -410,6 +441,7 @@ MPM_API mpm_status mpm_get_particles(mpm_ctx *ctx, float *x, float *v, float *C,
     }
     if (off > ctx->stage_bytes) return fail(ctx, MPM_ERR_CUDA, "internal: staging too small");
     launch_export(D, dptr[0], dptr[1], dptr[2], dptr[3], st);
+    ++ctx->launches;
     CKLAUNCH();
     for (int i = 0; i < 4; ++i)
         if (outs[i] && dptr[i] != outs[i])
@@ -422,13 +454,14 @@ MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream) {
     return check_device_error(ctx, S(stream));
 }
 
-MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[8], void *stream) {
+MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream) {
     if (!ctx || !counters) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
     CK(cudaStreamSynchronize(st));
     unsigned c[CTR_COUNT], err = 0;
     CK(cudaMemcpy(c, ctx->D.ctr, sizeof(c), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&err, ctx->D.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 16; ++i) counters[i] = 0;
     counters[0] = ctx->D.n;
     counters[1] = c[CTR_N_PLAN];
     counters[2] = std::max(c[CTR_N_ACTIVE], c[CTR_N_ACTIVE + 1]);
@@ -437,6 +470,30 @@ MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[8], void *stream) {
     counters[5] = ctx->recorded;
     counters[6] = err;
     counters[7] = ctx->pool_blocks;
+    counters[8] = ctx->launches;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_trace(mpm_ctx *ctx, int32_t enable, double ms[3], int64_t count[3]) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (ms && count) {
+        for (int m = 0; m < 3; ++m) {
+            ms[m] = 0.0;
+            count[m] = 0;
+            for (size_t u = 0; u + 1 < ctx->trace_used[m]; u += 2) {
+                float t = 0.f;
+                if (cudaEventSynchronize(ctx->trace_ev[m][u + 1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, ctx->trace_ev[m][u], ctx->trace_ev[m][u + 1]) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, MPM_ERR_CUDA, "trace: event query failed");
+                }
+                ms[m] += t;
+                count[m] += 1;
+            }
+        }
+    }
+    for (int m = 0; m < 3; ++m) ctx->trace_used[m] = 0;
+    ctx->trace_on = enable != 0;
     return MPM_OK;
 }
 
@@ -464,6 +521,8 @@ MPM_API mpm_status mpm_destroy(mpm_ctx *ctx) {
     dfree(ctx->mel); dfree(ctx->mpl);
     dfree(ctx->stage);
     free_adjoint(ctx->adj);
+    for (int m = 0; m < 3; ++m)
+        for (cudaEvent_t e : ctx->trace_ev[m]) cudaEventDestroy(e);
     delete ctx;
     return MPM_OK;
 }
@@ -480,14 +539,15 @@ MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream
     size_t nn = (size_t)ctx->total_blocks * BLK_NODES;
     CK(cudaMemsetAsync(m, 0, nn * sizeof(float), st));
     CK(cudaMemsetAsync(mv, 0, 3 * nn * sizeof(float), st));
-    launch_plan(D, 0, st);
-    launch_activate_sort(D, 0, 1, ctx->grid_small, st);
-    launch_substep(D, 0, 0, 0, ctx->grid_sub[0], ctx->threads, st);
+    L_plan(ctx, 0, st);
+    L_activate_sort(ctx, 0, 1, st);
+    L_substep(ctx, 0, 0, 0, st);
     launch_grid_dense(D, 0, 0, m, mv, st);
+    ++ctx->launches;
     // clear the momentum buffer again (the update zeroes it); the binning of
     // the current positions was consumed by the plan, so rebuild it
-    launch_grid_update(D, 0, -1, ctx->grid_small, st);
-    launch_bin(D, st);
+    L_grid_update(ctx, 0, -1, st);
+    L_bin(ctx, st);
     CKLAUNCH();
     return check_device_error(ctx, st);
 }

@@ -84,9 +84,21 @@ struct mpm_ctx {
     long long recorded = 0;       // substeps recorded since the last load / reset
     bool record_broken = false;
     mpm::AdjointStore adj;
+    // tracing: kernel launch count, and CUDA event pairs around substep kernels
+    long long launches = 0;
+    bool trace_on = false;
+    std::vector<cudaEvent_t> trace_ev[3];   // per substep mode: start, end, start, end, ...
+    size_t trace_used[3] = {0, 0, 0};
 };
 
 namespace mpm {
+// kernel launches through these wrappers are counted (and the substep kernel
+// timed when tracing is on)
+void L_plan(mpm_ctx *ctx, int bump_par, cudaStream_t st);
+void L_activate_sort(mpm_ctx *ctx, int par, int do_sort, cudaStream_t st);
+void L_grid_update(mpm_ctx *ctx, int par, int bump_par, cudaStream_t st, int keep_momentum = 0);
+void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
+void L_bin(mpm_ctx *ctx, cudaStream_t st);
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);

@@ -100,6 +100,9 @@ class Simulator:
     def stats(self, stream=None):
         return L.mpm_stats(self.ctx, _stream(stream))
 
+    def trace(self, enable):
+        return L.mpm_trace(self.ctx, enable)
+
     def record_reset(self):
         L.mpm_record_reset(self.ctx)
 
