@@ -167,6 +167,51 @@ MPM_API mpm_status mpm_trace(mpm_ctx *ctx, int32_t enable, double ms[3], int64_t
  * state is left unchanged.  Synchronises the stream. */
 MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * mpm_substep_noalloc -- one substep without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc.  Examples are an application whose device memory
+ * is fixed at start-up, code running while another allocator owns the
+ * device's memory, and latency-critical paths that cannot take the implicit
+ * device synchronisation of cudaMalloc / cudaFree.  It advances n particles by
+ * one substep (the same P2G with stress, grid update with walls, and G2P with
+ * the return map as mpm_step) on a dense grid of grid_res nodes, without a
+ * context.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Scratch: the grid lives in a file-scope device array of
+ * MPM_NOALLOC_MAX_NODES nodes (16 bytes each, 4 MiB), plus one error word;
+ * every GPU that loads libmpm holds this memory until the process exits.
+ * grid_res[0] * grid_res[1] * grid_res[2] above MPM_NOALLOC_MAX_NODES returns
+ * MPM_ERR_CAPACITY before any GPU work; more than MPM_NOALLOC_MAX_MATERIALS
+ * table entries return MPM_ERR_INVALID_ARG.
+ *
+ * Every call shares that scratch and finds the previous call's contents in
+ * it; each call clears the nodes and the error word it uses.  Calls whose GPU
+ * work overlaps (different streams, or different host threads on one device)
+ * race on the scratch: serialise them.
+ *
+ * The first call on a device looks up the scratch's device address for that
+ * device (host code cannot use the array's symbol directly); make that first
+ * call before any stream capture.
+ *
+ * Arguments: grid_res, dx, dt, gravity, table, n_materials as in mpm_create
+ * (table on the host); opt (nullable) supplies bound and walls.  x, v (n x 3),
+ * C, F (n x 9), vol (n), material_id (n) are device arrays; the outputs x_out,
+ * v_out (n x 3), C_out, F_out (n x 9) are device arrays and may alias the
+ * inputs.  Per-particle parameters come from the table only.  Synchronises
+ * the stream; returns MPM_ERR_OUT_OF_DOMAIN when a particle's stencil leaves
+ * the grid or a material id is out of range, MPM_ERR_NONFINITE on a
+ * non-finite result, MPM_ERR_INVALID_ARG for NULL or host pointers.
+ * ------------------------------------------------------------------------- */
+#define MPM_NOALLOC_MAX_NODES 262144      /* 64^3 */
+#define MPM_NOALLOC_MAX_MATERIALS 16
+MPM_API mpm_status mpm_substep_noalloc(const int32_t grid_res[3], float dx, float dt, const float gravity[3],
+                                       const mpm_material *table, int32_t n_materials, const mpm_options *opt,
+                                       int64_t n, const float *x, const float *v, const float *C, const float *F,
+                                       const float *vol, const int32_t *material_id, float *x_out, float *v_out,
+                                       float *C_out, float *F_out, void *stream);
+
 /* Last error message of this context (or of the last failed mpm_create when
  * ctx is NULL).  Static storage owned by the library. */
 MPM_API const char *mpm_last_error(const mpm_ctx *ctx);

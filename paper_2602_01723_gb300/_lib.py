@@ -56,6 +56,9 @@ SIGNATURES = {
     "mpm_destroy": (ctypes.c_int, [_ctx_p]),
     "mpm_debug_p2g": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     "mpm_trace": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _i64p]),
+    "mpm_substep_noalloc": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
+                                           ctypes.c_int32, ctypes.POINTER(mpm_options), ctypes.c_int64,
+                                           _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
