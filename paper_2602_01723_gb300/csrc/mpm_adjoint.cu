@@ -1,14 +1,569 @@
 // mpm_adjoint.cu -- recorded forward pass (checkpoints every ckpt_every
 // substeps) and the reverse pass of the MLS-MPM substep.
+//
+// Reverse of one substep (state S_s -> S_{s+1}), given the adjoint of S_{s+1}:
+//   recompute: bin S_s, P2G, grid update keeping (mv, m)
+//   k_adj_g2p : reverse of the return map, the F update, advection and the
+//               G2P gathers; scatters the grid-velocity adjoint and writes the
+//               partial adjoint of x and F
+//   k_adj_grid: reverse of v = mask (mv/m + dt g) per node
+//   k_adj_p2g : reverse of the P2G scatter and of the stress; completes the
+//               adjoint of x, v, C, F and adds the parameter gradients
+// The derivatives are taken by hand from the forward in mpm_forward.cu; the
+// SVD-based pieces use closed forms in the singular basis (see the comments
+// at plastic_adjoint and fcr_adjoint).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
 
 #include "mpm_internal.h"
+#include "mpm_math.cuh"
 
 namespace mpm {
 
+// adjoint state of one particle: 6 float4 = x(3) v(3) C(9) F(9)
+constexpr int ADJ_F4 = 6;
+
+// ---------------------------------------------------------------------------
+// device math of the reverse pass
+// ---------------------------------------------------------------------------
+
+// M = U Z V^T
+__device__ __forceinline__ void u_z_vt(float M[9], const float U[9], const float Z[9], const float V[9]) {
+    float T[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) T[3 * r + c] = U[3 * r] * Z[c] + U[3 * r + 1] * Z[3 + c] + U[3 * r + 2] * Z[6 + c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) M[3 * r + c] = T[3 * r] * V[3 * c] + T[3 * r + 1] * V[3 * c + 1] + T[3 * r + 2] * V[3 * c + 2];
+}
+// K = U^T M V
+__device__ __forceinline__ void ut_m_v(float K[9], const float U[9], const float M[9], const float V[9]) {
+    float T[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) T[3 * r + c] = U[r] * M[c] + U[3 + r] * M[3 + c] + U[6 + r] * M[6 + c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) K[3 * r + c] = T[3 * r] * V[c] + T[3 * r + 1] * V[3 + c] + T[3 * r + 2] * V[6 + c];
+}
+
+// Reverse of F_new = U diag(z(s)) V^T (the return map).  With K = U^T Fbar V:
+//   diagonal:     sbar_k = sum_i K_ii dz_i/ds_k   (plus the parameter terms)
+//   off-diagonal: Y_ij = K_ij (A+B)/2 + K_ji (A-B)/2,
+//                 A = (z_i - z_j)/(s_i - s_j), B = (z_i + z_j)/(s_i + s_j)
+//   Gbar = U (diag(sbar) + Y) V^T.
+// In the projected case z_i = exp(h_i) with h_i - h_j = c (eps_i - eps_j),
+// c = 1 - dgamma/|eps_hat|, so A = (z_j/s_j) expm1(c D)/expm1(D) with
+// D = eps_i - eps_j, whose limit as D -> 0 is the isotropic c z_j / s_j.
+__device__ void plastic_adjoint(int plastic, int rm, const float U[9], const float V[9], const float s[3],
+                                const float d[3], const float z[3], float mu, float lam, float yield, float alpha,
+                                const float Fbar[9], float Gbar[9], float &mubar, float &lambar, float &ybar) {
+    float K[9];
+    ut_m_v(K, U, Fbar, V);
+    float Y[9];
+    if (rm == RM_TIP) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Y[3 * i + j] = i == j ? 0.f : (K[3 * i + j] - K[3 * j + i]) / (s[i] + s[j]);
+        u_z_vt(Gbar, U, Y, V);
+        return;
+    }
+    // projected case
+    float eps[3], deps[3], tr = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const bool clamped = !(s[i] > MPM_SIGMA_FLOOR);
+        eps[i] = log_sigma(s[i], d[i]);
+        deps[i] = clamped ? 0.f : 1.f / s[i];
+        tr += eps[i];
+    }
+    const float m3 = tr * (1.f / 3.f);
+    const float e[3] = {eps[0] - m3, eps[1] - m3, eps[2] - m3};
+    const float nrm = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    float dg, ddg[3], ddg_mu, ddg_lam, ddg_y;
+    if (plastic == PLASTIC_VM) {
+        dg = nrm - yield / (2.f * mu);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ddg[k] = e[k] / nrm;
+        ddg_mu = yield / (2.f * mu * mu);
+        ddg_lam = 0.f;
+        ddg_y = -1.f / (2.f * mu);
+    } else {
+        const float kap = (3.f * lam + 2.f * mu) / (2.f * mu) * alpha;
+        dg = nrm + kap * tr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ddg[k] = e[k] / nrm + kap;
+        ddg_mu = tr * (-3.f * lam * alpha / (2.f * mu * mu));
+        ddg_lam = tr * (3.f * alpha / (2.f * mu));
+        ddg_y = 0.f;
+    }
+    const float inv_n = 1.f / nrm;
+    float Jz[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float Pik = (i == k ? 1.f : 0.f) - (1.f / 3.f);
+            const float dunit = (Pik - e[i] * e[k] * inv_n * inv_n) * inv_n;
+            const float dh = (i == k ? 1.f : 0.f) - ddg[k] * e[i] * inv_n - dg * dunit;
+            Jz[3 * i + k] = z[i] * dh * deps[k];
+        }
+    float sb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sb[k] = K[0] * Jz[k] + K[4] * Jz[3 + k] + K[8] * Jz[6 + k];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float f = -z[i] * e[i] * inv_n * K[4 * i];
+        mubar += f * ddg_mu;
+        lambar += f * ddg_lam;
+        ybar += f * ddg_y;
+    }
+    const float c = 1.f - dg * inv_n;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) { Y[4 * i] = sb[i]; continue; }
+            float A;
+            if (s[i] > MPM_SIGMA_FLOOR && s[j] > MPM_SIGMA_FLOOR) {
+                const float D = eps[i] - eps[j];
+                const float phi = fabsf(D) < 1e-3f ? c * (1.f + 0.5f * (c - 1.f) * D) : expm1f(c * D) / expm1f(D);
+                A = z[j] / s[j] * phi;
+            } else {
+                A = (z[i] - z[j]) / (s[i] - s[j]);
+            }
+            const float B = (z[i] + z[j]) / (s[i] + s[j]);
+            Y[3 * i + j] = K[3 * i + j] * 0.5f * (A + B) + K[3 * j + i] * 0.5f * (A - B);
+        }
+    u_z_vt(Gbar, U, Y, V);
+}
+
+// Reverse of the fixed-corotated Kirchhoff stress tau = 2 mu (F - R) F^T +
+// lam J (J - 1) I for a symmetric adjoint T, in the singular basis of F:
+// with W = U^T T U,
+//   Z_ii = 2 mu W_ii (s_i + e_i) + Jbar prod_{k != i} s_k,  Jbar = lam tr(T) (2J - 1)
+//   Z_ij = 2 mu W_ij [(s_j + e_j) - (s_j - s_i)/(s_i + s_j)]  (i != j)
+//   Fbar += U Z V^T,  mubar += 2 sum_i e_i s_i W_ii,  lambar += tr(T) J (J - 1).
+// (The (s_j - s_i)/(s_i + s_j) term is the reverse of the polar rotation.)
+__device__ void fcr_adjoint(const float U[9], const float V[9], const float s[3], const float e[3], float mu,
+                            float lam, const float T[9], float Fbar[9], float &mubar, float &lambar) {
+    float W[9];
+    ut_m_v(W, U, T, U);
+    const float jm1 = e[0] + e[1] + e[2] + e[0] * e[1] + e[0] * e[2] + e[1] * e[2] + e[0] * e[1] * e[2];
+    const float J = 1.f + jm1;
+    const float trT = T[0] + T[4] + T[8];
+    const float Jbar = lam * trT * (2.f * J - 1.f);
+    float Z[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (i == j) {
+                const float po = s[(i + 1) % 3] * s[(i + 2) % 3];
+                Z[4 * i] = 2.f * mu * W[4 * i] * (s[i] + e[i]) + Jbar * po;
+            } else {
+                Z[3 * i + j] = 2.f * mu * W[3 * i + j] * ((s[j] + e[j]) - (s[j] - s[i]) / (s[i] + s[j]));
+            }
+        }
+    float D[9];
+    u_z_vt(D, U, Z, V);
+#pragma unroll
+    for (int t = 0; t < 9; ++t) Fbar[t] += D[t];
+    mubar += 2.f * (e[0] * s[0] * W[0] + e[1] * s[1] * W[4] + e[2] * s[2] * W[8]);
+    lambar += trT * J * jm1;
+}
+
+// Reverse of the Neo-Hookean Kirchhoff stress tau = mu (F F^T - I) + lam log J I:
+//   Fbar += 2 mu T F + lam tr(T) F^{-T};  mubar += <T, F F^T - I>;  lambar += tr(T) log J
+__device__ void nh_adjoint(const float F[9], float mu, float lam, const float T[9], float Fbar[9], float &mubar,
+                           float &lambar) {
+    const float cof[9] = {F[4] * F[8] - F[5] * F[7], F[5] * F[6] - F[3] * F[8], F[3] * F[7] - F[4] * F[6],
+                          F[2] * F[7] - F[1] * F[8], F[0] * F[8] - F[2] * F[6], F[1] * F[6] - F[0] * F[7],
+                          F[1] * F[5] - F[2] * F[4], F[2] * F[3] - F[0] * F[5], F[0] * F[4] - F[1] * F[3]};
+    const float jm1 = det_minus_one(F);
+    const float J = 1.f + jm1;
+    const float trT = T[0] + T[4] + T[8];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            Fbar[3 * r + c] += 2.f * mu * (T[3 * r] * F[c] + T[3 * r + 1] * F[3 + c] + T[3 * r + 2] * F[6 + c]) +
+                               lam * trT * cof[3 * r + c] / J;
+    // <T, F F^T - I> with F F^T - I = H + H^T + H H^T, H = F - I
+    float h[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) h[t] = F[t];
+    h[0] -= 1.f; h[4] -= 1.f; h[8] -= 1.f;
+    float acc = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ffi = h[3 * i + j] + h[3 * j + i] + h[3 * i] * h[3 * j] + h[3 * i + 1] * h[3 * j + 1] +
+                              h[3 * i + 2] * h[3 * j + 2];
+            acc += T[3 * i + j] * ffi;
+        }
+    mubar += acc;
+    lambar += trT * log1pf(jm1);
+}
+
+// (mubar, lambar) -> (d/d log E, d/d nu), with E and nu recovered from mu, lambda
+__device__ __forceinline__ void lame_chain(float mu, float lam, float mubar, float lambar, float &gE, float &gnu) {
+    const float nu = lam / (2.f * (lam + mu));
+    gE = mubar * mu + lambar * lam;
+    const float q = 1.f - 2.f * nu;
+    gnu = mubar * (-mu / (1.f + nu)) + lambar * (2.f * mu * (1.f + 2.f * nu * nu) / ((1.f + nu) * q * q));
+}
+
+// ---------------------------------------------------------------------------
+// reverse kernels (chunked like the forward: particles of one 4^3 block)
+// ---------------------------------------------------------------------------
+constexpr int GT = 6, GT3 = 216;
+constexpr int ADJ_THREADS = 128;
+
+__device__ __forceinline__ int page_slot_a(const Dev &D, int par, unsigned ep, int inst, int bx, int by, int bz) {
+    if (bx < 0 || by < 0 || bz < 0 || bx >= D.NB[0] || by >= D.NB[1] || bz >= D.NB[2]) return -1;
+    const unsigned k = block_key(D, inst, bx, by, bz);
+    return D.page_epoch[par][k] == ep ? D.page[par][k] : -1;
+}
+__device__ __forceinline__ int node_loc(int I, int J, int K) { return ((I & 3) * 4 + (J & 3)) * 4 + (K & 3); }
+
+// loads the 6^3-node tile (blocks B .. B+1) of pool `src` into shared memory
+__device__ void load_tile(const Dev &D, const float4 *src, unsigned ep, int inst, int bx, int by, int bz,
+                          float4 *tile, int *slots) {
+    if (threadIdx.x < 8) {
+        const int o = threadIdx.x;
+        slots[o] = page_slot_a(D, 0, ep, inst, bx + (o >> 2), by + ((o >> 1) & 1), bz + (o & 1));
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < GT3; t += blockDim.x) {
+        const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+        const int sl = slots[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+        tile[t] = sl >= 0 ? src[(size_t)sl * BLK_NODES + node_loc(i, j, k)] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncthreads();
+}
+
+struct ParticleIn {
+    float x[3], v[3], C[9], F[9];
+    float mass, vol, mu, lam, yield, alpha;
+    int elastic, plastic;
+};
+__device__ __forceinline__ void load_particle(const float4 *r, ParticleIn &P) {
+    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7];
+    P.x[0] = r0.x; P.x[1] = r0.y; P.x[2] = r0.z; P.mass = r0.w;
+    P.v[0] = r1.x; P.v[1] = r1.y; P.v[2] = r1.z; P.vol = r1.w;
+    P.C[0] = r2.x; P.C[1] = r2.y; P.C[2] = r2.z; P.C[3] = r2.w;
+    P.C[4] = r3.x; P.C[5] = r3.y; P.C[6] = r3.z; P.C[7] = r3.w; P.C[8] = r4.x;
+    P.F[0] = r4.y; P.F[1] = r4.z; P.F[2] = r4.w; P.F[3] = r5.x; P.F[4] = r5.y; P.F[5] = r5.z; P.F[6] = r5.w;
+    P.F[7] = r6.x; P.F[8] = r6.y;
+    P.mu = r6.z; P.lam = r6.w; P.yield = r7.x;
+    const int info = __float_as_int(r7.y);
+    P.elastic = info & 15;
+    P.plastic = (info >> 4) & 15;
+    P.alpha = r7.w;
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
+                                                         float4 *gpar, float4 *gbar) {
+    __shared__ float4 s_g[GT3];
+    __shared__ int s_slot[8];
+    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
+    const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
+    const float c4 = 4.f * inv_dx * inv_dx;
+    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const int4 ch = D.chunks[c];
+        int inst, bx, by, bz;
+        key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+        load_tile(D, D.gv[0], ep, inst, bx, by, bz, s_g, s_slot);
+        for (int j = threadIdx.x; j < ch.z; j += blockDim.x) {
+            const unsigned p = D.sorted[ch.y + j];
+            ParticleIn P;
+            load_particle(D.rec + (size_t)p * REC_F4, P);
+            float f[3];
+            int b[3];
+            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
+            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
+            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
+            if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); continue; }
+            float w[3][3], dw[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
+            // recompute v' and C'
+            float vn[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int i = 0; i < 3; ++i)
+                for (int jj = 0; jj < 3; ++jj)
+                    for (int k = 0; k < 3; ++k) {
+                        const float wt = w[0][i] * w[1][jj] * w[2][k];
+                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float dd[3] = {(float)i - f[0], (float)jj - f[1], (float)k - f[2]};
+                        const float a3[3] = {wt * g.x, wt * g.y, wt * g.z};
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            vn[r] += a3[r];
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) Bm[3 * r + cc] += a3[r] * dd[cc];
+                        }
+                    }
+            float Cn[9], G[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) Cn[t] = 4.f * inv_dx * Bm[t];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc)
+                    G[3 * r + cc] = P.F[3 * r + cc] + dt * (Cn[3 * r] * P.F[cc] + Cn[3 * r + 1] * P.F[3 + cc] +
+                                                            Cn[3 * r + 2] * P.F[6 + cc]);
+            // adjoint of the new state
+            const float4 *ap = ain + (size_t)p * ADJ_F4;
+            const float4 a0 = ap[0], a1 = ap[1], a2 = ap[2], a3v = ap[3], a4 = ap[4], a5 = ap[5];
+            const float xb[3] = {a0.x, a0.y, a0.z};
+            const float vb[3] = {a0.w, a1.x, a1.y};
+            const float Cb[9] = {a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3v.x, a3v.y, a3v.z};
+            const float Fb[9] = {a3v.w, a4.x, a4.y, a4.z, a4.w, a5.x, a5.y, a5.z, a5.w};
+            // reverse of the return map
+            float Gb[9];
+#pragma unroll
+            for (int t = 0; t < 9; ++t) Gb[t] = Fb[t];
+            float mubar = 0.f, lambar = 0.f, ybar = 0.f;
+            if (P.plastic != PLASTIC_NONE) {
+                float U[9], V[9], s3[3], e3[3], d3[3], z[3], ze[3];
+                svd3_robust(G, U, V, s3, e3, d3);
+                const int rm = return_map(P.plastic, s3, e3, d3, P.mu, P.lam, P.yield, P.alpha, z, ze);
+                if (rm != RM_ELASTIC)
+                    plastic_adjoint(P.plastic, rm, U, V, s3, d3, z, P.mu, P.lam, P.yield, P.alpha, Fb, Gb, mubar,
+                                    lambar, ybar);
+            }
+            // G = (I + dt C') F
+            float Ct[9], Fp[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    Ct[3 * r + cc] = Cb[3 * r + cc] + dt * (Gb[3 * r] * P.F[3 * cc] + Gb[3 * r + 1] * P.F[3 * cc + 1] +
+                                                             Gb[3 * r + 2] * P.F[3 * cc + 2]);
+                    Fp[3 * r + cc] = Gb[3 * r + cc] + dt * (Cn[r] * Gb[cc] + Cn[3 + r] * Gb[3 + cc] + Cn[6 + r] * Gb[6 + cc]);
+                }
+            // x' = x + dt v'
+            float xa[3] = {xb[0], xb[1], xb[2]};
+            const float vt[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
+            // reverse of the gathers
+            for (int i = 0; i < 3; ++i)
+                for (int jj = 0; jj < 3; ++jj)
+                    for (int k = 0; k < 3; ++k) {
+                        const float wt = w[0][i] * w[1][jj] * w[2][k];
+                        const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
+                                             w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
+                        const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
+                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float vi[3] = {g.x, g.y, g.z};
+                        float cd[3], wbar = 0.f;
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            cd[r] = Ct[3 * r] * dp[0] + Ct[3 * r + 1] * dp[1] + Ct[3 * r + 2] * dp[2];
+                            wbar += vt[r] * vi[r] + c4 * vi[r] * cd[r];
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            const float dpb = c4 * wt * (Ct[cc] * vi[0] + Ct[3 + cc] * vi[1] + Ct[6 + cc] * vi[2]);
+                            xa[cc] += wbar * gw[cc] - dpb;
+                        }
+                        const int sl = s_slot[(((b[0] + i) >> 2) << 2) | (((b[1] + jj) >> 2) << 1) | ((b[2] + k) >> 2)];
+                        if (sl >= 0)
+                            red_add_v4(gbar + (size_t)sl * BLK_NODES + node_loc(b[0] + i, b[1] + jj, b[2] + k),
+                                       wt * (vt[0] + c4 * cd[0]), wt * (vt[1] + c4 * cd[1]), wt * (vt[2] + c4 * cd[2]), 0.f);
+                        else
+                            set_err(D, ERRB_CAPACITY);
+                    }
+            float4 *op = aout + (size_t)p * ADJ_F4;
+            op[0] = make_float4(xa[0], xa[1], xa[2], 0.f);
+            op[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            op[2] = make_float4(0.f, 0.f, 0.f, 0.f);
+            op[3] = make_float4(0.f, 0.f, 0.f, Fp[0]);
+            op[4] = make_float4(Fp[1], Fp[2], Fp[3], Fp[4]);
+            op[5] = make_float4(Fp[5], Fp[6], Fp[7], Fp[8]);
+            float gE, gnu;
+            lame_chain(P.mu, P.lam, mubar, lambar, gE, gnu);
+            float4 g4 = gpar[p];
+            g4.x += gE; g4.y += gnu; g4.z += ybar;
+            gpar[p] = g4;
+        }
+        __syncthreads();
+    }
+}
+
+// reverse of the grid update, per active node: ubar = mask * vbar,
+// Pbar = ubar / m, mbar = -(ubar . P) / m^2; also clears the momentum pool
+__global__ void k_adj_grid(Dev D, float4 *gbar) {
+    const unsigned total = min(D.ctr[CTR_N_ACTIVE + 0], D.max_active) * BLK_NODES;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const float4 a = D.gmv[0][i];
+        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (a.w > 0.f) {
+            const unsigned slot = i >> 6, l = i & 63u;
+            int inst, bx, by, bz;
+            key_coords(D, D.active[0][slot], inst, bx, by, bz);
+            const int idx[3] = {bx * BLK + (int)(l >> 4), by * BLK + (int)((l >> 2) & 3u), bz * BLK + (int)(l & 3u)};
+            const float im = 1.f / a.w;
+            const float u[3] = {a.x * im + D.dt * D.g[0], a.y * im + D.dt * D.g[1], a.z * im + D.dt * D.g[2]};
+            float mask[3] = {1.f, 1.f, 1.f};
+            bool sticky = false;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (idx[d] < D.bound && D.wall[2 * d] == 2) sticky = true;
+                if (idx[d] >= D.R[d] - D.bound && D.wall[2 * d + 1] == 2) sticky = true;
+            }
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (sticky) mask[d] = 0.f;
+                if (idx[d] < D.bound && D.wall[2 * d] == 1 && u[d] < 0.f) mask[d] = 0.f;
+                if (idx[d] >= D.R[d] - D.bound && D.wall[2 * d + 1] == 1 && u[d] > 0.f) mask[d] = 0.f;
+            }
+            const float4 vb = gbar[i];
+            const float ub[3] = {mask[0] * vb.x, mask[1] * vb.y, mask[2] * vb.z};
+            out = make_float4(ub[0] * im, ub[1] * im, ub[2] * im, -(ub[0] * a.x + ub[1] * a.y + ub[2] * a.z) * im * im);
+        }
+        gbar[i] = out;
+        D.gmv[0][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
+    __shared__ float4 s_g[GT3];
+    __shared__ int s_slot[8];
+    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
+    const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
+    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        const int4 ch = D.chunks[c];
+        int inst, bx, by, bz;
+        key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+        load_tile(D, gbar, ep, inst, bx, by, bz, s_g, s_slot);
+        for (int j = threadIdx.x; j < ch.z; j += blockDim.x) {
+            const unsigned p = D.sorted[ch.y + j];
+            ParticleIn P;
+            load_particle(D.rec + (size_t)p * REC_F4, P);
+            float f[3];
+            int b[3];
+            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
+            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
+            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
+            if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); continue; }
+            float w[3][3], dw[3][3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
+            // recompute the stress and the affine momentum A = m C - k tau
+            float U[9], V[9], s3[3], e3[3], d3[3];
+            Sym tau;
+            if (P.elastic == 0) {
+                svd3_robust(P.F, U, V, s3, e3, d3);
+                tau = tau_fcr(U, s3, e3, P.mu, P.lam);
+            } else if (!tau_nh(P.F, P.mu, P.lam, tau)) {
+                tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            }
+            const float kf = 4.f * dt * P.vol * inv_dx * inv_dx;
+            const float A[9] = {P.mass * P.C[0] - kf * tau.xx, P.mass * P.C[1] - kf * tau.xy,
+                                P.mass * P.C[2] - kf * tau.xz, P.mass * P.C[3] - kf * tau.xy,
+                                P.mass * P.C[4] - kf * tau.yy, P.mass * P.C[5] - kf * tau.yz,
+                                P.mass * P.C[6] - kf * tau.xz, P.mass * P.C[7] - kf * tau.yz,
+                                P.mass * P.C[8] - kf * tau.zz};
+            float xa[3] = {0.f, 0.f, 0.f}, va[3] = {0.f, 0.f, 0.f};
+            float Ab[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int i = 0; i < 3; ++i)
+                for (int jj = 0; jj < 3; ++jj)
+                    for (int k = 0; k < 3; ++k) {
+                        const float wt = w[0][i] * w[1][jj] * w[2][k];
+                        const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
+                                             w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
+                        const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
+                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float Pb[3] = {g.x, g.y, g.z};
+                        float wbar = g.w * P.mass;
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            const float Adr = A[3 * r] * dp[0] + A[3 * r + 1] * dp[1] + A[3 * r + 2] * dp[2];
+                            wbar += Pb[r] * (P.mass * P.v[r] + Adr);
+                            va[r] += wt * P.mass * Pb[r];
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) Ab[3 * r + cc] += wt * Pb[r] * dp[cc];
+                        }
+#pragma unroll
+                        for (int cc = 0; cc < 3; ++cc) {
+                            const float dpb = wt * (A[cc] * Pb[0] + A[3 + cc] * Pb[1] + A[6 + cc] * Pb[2]);
+                            xa[cc] += wbar * gw[cc] - dpb;
+                        }
+                    }
+            // C enters A as m C; tau as -k tau (tau symmetric: use the symmetric part)
+            float T[9];
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) T[3 * r + cc] = -0.5f * kf * (Ab[3 * r + cc] + Ab[3 * cc + r]);
+            float Fb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            float mubar = 0.f, lambar = 0.f;
+            if (P.elastic == 0) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
+            else nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
+            float4 *op = aout + (size_t)p * ADJ_F4;
+            const float4 o0 = op[0], o3 = op[3], o4 = op[4], o5 = op[5];
+            op[0] = make_float4(o0.x + xa[0], o0.y + xa[1], o0.z + xa[2], va[0]);
+            op[1] = make_float4(va[1], va[2], P.mass * Ab[0], P.mass * Ab[1]);
+            op[2] = make_float4(P.mass * Ab[2], P.mass * Ab[3], P.mass * Ab[4], P.mass * Ab[5]);
+            op[3] = make_float4(P.mass * Ab[6], P.mass * Ab[7], P.mass * Ab[8], o3.w + Fb[0]);
+            op[4] = make_float4(o4.x + Fb[1], o4.y + Fb[2], o4.z + Fb[3], o4.w + Fb[4]);
+            op[5] = make_float4(o5.x + Fb[5], o5.y + Fb[6], o5.z + Fb[7], o5.w + Fb[8]);
+            float gE, gnu;
+            lame_chain(P.mu, P.lam, mubar, lambar, gE, gnu);
+            float4 g4 = gpar[p];
+            g4.x += gE; g4.y += gnu;
+            gpar[p] = g4;
+        }
+        __syncthreads();
+    }
+}
+
+// clears the grid-adjoint pool of the active blocks
+__global__ void k_adj_clear(Dev D, float4 *gbar) {
+    const unsigned total = min(D.ctr[CTR_N_ACTIVE + 0], D.max_active) * BLK_NODES;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x)
+        gbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// adjoint of positions += dL/dx of one frame
+__global__ void k_inject(int n, float4 *adj, const float *dLdx) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        float4 a = adj[(size_t)p * ADJ_F4];
+        a.x += dLdx[3 * p];
+        a.y += dLdx[3 * p + 1];
+        a.z += dLdx[3 * p + 2];
+        adj[(size_t)p * ADJ_F4] = a;
+    }
+}
+
+__global__ void k_export_grads(int n, const float4 *gpar, const float4 *adj, float *dparams, float *dstate0) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        const float4 g = gpar[p];
+        dparams[3 * p] = g.x;
+        dparams[3 * p + 1] = g.y;
+        dparams[3 * p + 2] = g.z;
+        if (dstate0) {
+            const float *a = reinterpret_cast<const float *>(adj + (size_t)p * ADJ_F4);
+            for (int t = 0; t < 24; ++t) dstate0[24 * p + t] = a[t];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
 void free_adjoint(AdjointStore &a) {
     for (float4 *p : a.ckpt)
         if (p) cudaFree(p);
@@ -19,15 +574,17 @@ void free_adjoint(AdjointStore &a) {
     if (a.gpar) cudaFree(a.gpar);
     if (a.gbar) cudaFree(a.gbar);
     if (a.frames) cudaFree(a.frames);
+    if (a.final_state) cudaFree(a.final_state);
     a = AdjointStore();
 }
 
 static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
-    size_t bytes = (size_t)ctx->cap * REC_F4 * sizeof(float4);
+    const size_t bytes = (size_t)ctx->cap * REC_F4 * sizeof(float4);
     if (A.ckpt.size() <= c) A.ckpt.resize(c + 1, nullptr);
     if (!A.ckpt[c] || A.cap != ctx->cap) {
         if (A.ckpt[c]) cudaFree(A.ckpt[c]);
+        A.ckpt[c] = nullptr;
         cudaError_t e = cudaMalloc(&A.ckpt[c], bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
@@ -45,28 +602,177 @@ static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
     if (ctx->record_broken)
         return ctx_fail(ctx, MPM_ERR_STATE, "recording interrupted by an unrecorded step; call mpm_record_reset");
+    if (ctx->adj.cap != ctx->cap && !ctx->adj.ckpt.empty()) {
+        for (float4 *p : ctx->adj.ckpt)
+            if (p) cudaFree(p);
+        ctx->adj.ckpt.clear();
+    }
     const long long k = ctx->opt.ckpt_every;
     int remaining = n_sub;
     while (remaining > 0) {
         if (ctx->recorded % k == 0) {
             mpm_status s = save_checkpoint(ctx, (size_t)(ctx->recorded / k), st);
             if (s) return s;
+            ctx->adj.cap = ctx->cap;
         }
-        int seg = (int)std::min<long long>(remaining, k - ctx->recorded % k);
+        const int seg = (int)std::min<long long>(remaining, k - ctx->recorded % k);
         mpm_status s = run_substeps(ctx, seg, st);
         if (s) return s;
         ctx->recorded += seg;
         remaining -= seg;
     }
-    ctx->adj.cap = ctx->cap;
     return MPM_OK;
+}
+
+template <typename T>
+static mpm_status dev_alloc(mpm_ctx *ctx, T **p, size_t count) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return ctx_fail(ctx, MPM_ERR_OOM, "reverse-pass allocation failed");
+    }
+    return MPM_OK;
+}
+
+// consume any pending binning, then bin the current records
+static void rebin(mpm_ctx *ctx, cudaStream_t st) {
+    L_plan(ctx, -1, st);
+    L_bin(ctx, st);
+}
+
+// reverse of one substep whose input state is `state`
+static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *aout, cudaStream_t st) {
+    Dev &D = ctx->D;
+    AdjointStore &A = ctx->adj;
+    float4 *saved = D.rec;
+    D.rec = state;
+    rebin(ctx, st);
+    L_plan(ctx, 0, st);
+    L_activate_sort(ctx, 0, 1, st);
+    L_substep(ctx, 0, 0, 0, st);                       // P2G of the recorded state
+    L_grid_update(ctx, 0, -1, st, 1);                  // v = mask(mv/m + dt g), keeping (mv, m)
+    const int grid = ctx->grid_sub[1];
+    k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
+    k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);
+    k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
+    k_adj_clear<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);
+    ctx->launches += 4;
+    D.rec = saved;
 }
 
 }  // namespace mpm
 
+using namespace mpm;
+
 extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const int32_t *frame_substep,
                                            const float *dL_dx, float *dL_dparams, float *dL_dstate0, void *stream) {
-    (void)n_frames; (void)frame_substep; (void)dL_dx; (void)dL_dparams; (void)dL_dstate0; (void)stream;
     if (!ctx) return MPM_ERR_INVALID_ARG;
-    return mpm::ctx_fail(ctx, MPM_ERR_STATE, "reverse pass not built yet");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ctx->loaded || ctx->sticky) return ctx_fail(ctx, MPM_ERR_STATE, "no valid particle state");
+    if (ctx->record_broken) return ctx_fail(ctx, MPM_ERR_STATE, "the recording was interrupted by an unrecorded step");
+    const long long S = ctx->recorded;
+    if (S <= 0) return ctx_fail(ctx, MPM_ERR_STATE, "nothing recorded: call mpm_step with record != 0 first");
+    if (n_frames < 0 || (n_frames > 0 && (!frame_substep || !dL_dx)) || !dL_dparams)
+        return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "bad frames / gradient arguments");
+    for (int f = 0; f < n_frames; ++f)
+        if (frame_substep[f] < 0 || frame_substep[f] > S)
+            return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "frame_substep outside [0, recorded substeps]");
+    Dev &D = ctx->D;
+    AdjointStore &A = ctx->adj;
+    const size_t n = (size_t)D.n;
+    const long long k = ctx->opt.ckpt_every;
+    mpm_status s;
+    if (A.cap_adj != ctx->cap) {
+        if ((s = dev_alloc(ctx, &A.adj[0], (size_t)ctx->cap * ADJ_F4)) || (s = dev_alloc(ctx, &A.adj[1], (size_t)ctx->cap * ADJ_F4)) ||
+            (s = dev_alloc(ctx, &A.gpar, (size_t)ctx->cap)) || (s = dev_alloc(ctx, &A.final_state, (size_t)ctx->cap * REC_F4))) {
+            A.cap_adj = 0;
+            return s;
+        }
+        A.cap_adj = ctx->cap;
+    }
+    if (A.pool != ctx->pool_blocks) {
+        if ((s = dev_alloc(ctx, &A.gbar, (size_t)ctx->pool_blocks * BLK_NODES))) { A.pool = 0; return s; }
+        A.pool = ctx->pool_blocks;
+        if (cudaMemsetAsync(A.gbar, 0, (size_t)A.pool * BLK_NODES * sizeof(float4), st) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "memset");
+    }
+    const size_t tape_states = (size_t)std::min<long long>(k, S);
+    if (A.tape_states < tape_states || A.tape_cap != ctx->cap) {
+        if ((s = dev_alloc(ctx, &A.tape, tape_states * (size_t)ctx->cap * REC_F4))) { A.tape_states = 0; return s; }
+        A.tape_states = tape_states;
+        A.tape_cap = ctx->cap;
+    }
+    // stage dL/dx
+    const size_t fbytes = (size_t)n_frames * n * 3 * sizeof(float);
+    const float *dldx = dL_dx;
+    if (n_frames > 0 && !is_device_ptr(dL_dx)) {
+        if (A.frames_bytes < fbytes) {
+            if ((s = dev_alloc(ctx, &A.frames, fbytes / sizeof(float)))) { A.frames_bytes = 0; return s; }
+            A.frames_bytes = fbytes;
+        }
+        if (cudaMemcpyAsync(A.frames, dL_dx, fbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "dL_dx copy");
+        dldx = A.frames;
+    }
+    if (cudaMemcpyAsync(A.final_state, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(A.adj[0], 0, n * ADJ_F4 * sizeof(float4), st) != cudaSuccess ||
+        cudaMemsetAsync(A.gpar, 0, n * sizeof(float4), st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
+    int cur = 0;
+    const int pg = grid_for((long long)n, 256);
+    auto inject = [&](long long sub) {
+        for (int f = 0; f < n_frames; ++f)
+            if (frame_substep[f] == sub) {
+                k_inject<<<pg, 256, 0, st>>>((int)n, A.adj[cur], dldx + (size_t)f * n * 3);
+                ++ctx->launches;
+            }
+    };
+    const long long nseg = (S + k - 1) / k;
+    for (long long c = nseg - 1; c >= 0; --c) {
+        const long long s0 = c * k;
+        const int len = (int)std::min<long long>(k, S - s0);
+        // recompute the segment's input states
+        if (cudaMemcpyAsync(D.rec, A.ckpt[(size_t)c], n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
+        rebin(ctx, st);
+        for (int j = 0; j < len; ++j) {
+            if (cudaMemcpyAsync(A.tape + (size_t)j * ctx->cap * REC_F4, D.rec, n * REC_F4 * sizeof(float4),
+                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
+            if (j < len - 1 && (s = run_substeps(ctx, 1, st))) return s;
+        }
+        // reverse through the segment
+        for (int j = len - 1; j >= 0; --j) {
+            inject(s0 + j + 1);
+            adjoint_substep(ctx, A.tape + (size_t)j * ctx->cap * REC_F4, A.adj[cur], A.adj[cur ^ 1], st);
+            cur ^= 1;
+        }
+    }
+    inject(0);
+    // outputs
+    float *dp = dL_dparams, *ds = dL_dstate0;
+    const bool dp_dev = is_device_ptr(dL_dparams), ds_dev = !dL_dstate0 || is_device_ptr(dL_dstate0);
+    if (!dp_dev || !ds_dev) {
+        // host outputs go through the context's staging buffer (>= 30 floats per particle)
+        float *tmp = reinterpret_cast<float *>(ctx->stage);
+        if (!dp_dev) dp = tmp;
+        if (!ds_dev) ds = tmp + ((n * 3 + 63) & ~size_t(63));
+    }
+    k_export_grads<<<pg, 256, 0, st>>>((int)n, A.gpar, A.adj[cur], dp, ds);
+    ++ctx->launches;
+    if (!dp_dev && cudaMemcpyAsync(dL_dparams, dp, n * 3 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "gradient copy");
+    if (dL_dstate0 && !ds_dev &&
+        cudaMemcpyAsync(dL_dstate0, ds, n * 24 * sizeof(float), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "state adjoint copy");
+
+    // restore the recorded end state and its binning
+    if (cudaMemcpyAsync(D.rec, A.final_state, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "state restore");
+    rebin(ctx, st);
+    if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, MPM_ERR_CUDA, "reverse-pass launch failed");
+    return ctx_check(ctx, st);
 }

@@ -50,10 +50,13 @@ struct AdjointStore {
     float4 *adj[2] = {nullptr, nullptr};   // adjoint state (x v C F) per particle, 6 float4
     float4 *gpar = nullptr;         // parameter gradients per particle (log E, nu, yield, 0)
     float4 *gbar = nullptr;         // grid adjoint pool
+    float4 *final_state = nullptr;  // recorded end state, restored after the reverse pass
     float *frames = nullptr;        // staged dL/dx
     size_t frames_bytes = 0;
-    long long cap = 0;
-    unsigned pool = 0;
+    long long cap = 0;              // particle capacity the checkpoints were sized for
+    long long cap_adj = 0;          // particle capacity of adj / gpar / final_state
+    long long tape_cap = 0;         // particle capacity of the tape
+    unsigned pool = 0;              // grid-adjoint pool capacity (blocks)
 };
 void free_adjoint(AdjointStore &a);
 

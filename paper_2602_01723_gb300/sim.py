@@ -131,3 +131,40 @@ class Simulator:
             self.close()
         except Exception:
             pass
+
+
+class Trajectory(torch.autograd.Function):
+    """Positions at loss frames as a differentiable function of per-particle
+    material parameters (log E, nu, yield stress), through libmpm's
+    hand-written adjoint with checkpoint recompute.
+
+    forward(params (n,3), sim, init, frame_sub) loads the initial state
+    `init` (dict with x, vol, mat_id and optionally v, C, F, instance) with
+    `params`, runs a recorded forward pass and returns x at the frames,
+    shape (n_frames, n, 3).  backward returns dL/dparams (n,3)."""
+
+    @staticmethod
+    def forward(ctx, params, sim, init, frame_sub):
+        frame_sub = [int(f) for f in frame_sub]
+        if sorted(frame_sub) != frame_sub or (frame_sub and frame_sub[0] < 0):
+            raise ValueError("frame_sub must be non-decreasing and >= 0")
+        sim.load(init["x"], init["vol"], init["mat_id"], v=init.get("v"), C=init.get("C"), F=init.get("F"),
+                 instance=init.get("instance"), params=params.detach())
+        frames, prev = [], 0
+        for f in frame_sub:
+            if f > prev:
+                sim.step(f - prev, record=True)
+            frames.append(sim.positions())
+            prev = f
+        ctx.sim = sim
+        ctx.frame_sub = frame_sub
+        return torch.stack(frames)
+
+    @staticmethod
+    def backward(ctx, grad_frames):
+        g = ctx.sim.backward(ctx.frame_sub, grad_frames.contiguous())
+        return g, None, None, None
+
+
+def trajectory(params, sim, init, frame_sub):
+    return Trajectory.apply(params, sim, init, frame_sub)
