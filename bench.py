@@ -39,6 +39,12 @@ WORKLOAD = "three_objects_300k"
 FWD_BYTES_PER_PS = 200.0
 ORACLE_SAMPLE_SUBSTEPS = 30
 REF_STEP_SUBSTEPS = 4
+FB_WORKLOAD = "ball_50k"
+# fwd+bwd algorithmic bytes per particle-substep: the forward (200 B), the
+# recompute of the checkpoint segment with the tape write (~200 B), and the
+# reverse substep (tape state read by the recomputed P2G, the G2P adjoint and
+# the P2G adjoint, adjoint state in and out, parameter gradients: ~480 B)
+FB_BYTES_PER_PS = 880.0
 
 
 def load_peaks():
@@ -272,6 +278,8 @@ def run_ours(args):
         err["x_one_substep_max_dx"] = float(np.abs(got[idx] - ref["x"]).max() / sc.dx)
         err["note"] = "teacher-forced: FP32 GPU vs FP64 oracle from the same state after %d substeps" % S
 
+    fb = fwd_bwd(args, dev, flush, world, dist)
+
     if rank == 0:
         cpu_v, cpu_t = oracle_rate(sc, ORACLE_SAMPLE_SUBSTEPS)
         line = {
@@ -294,12 +302,73 @@ def run_ours(args):
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "err_vs_fp64": err,
+            "fwd_bwd": fb,
         }
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fwd_bwd(args, dev, flush, world, dist):
+    """fwd+bwd throughput on the 50k-particle differentiable ball: one step =
+    a recorded 400-substep forward (checkpoint every 20) plus the reverse pass
+    for the 10-frame position MSE against a target run with the seeded
+    ground-truth parameters."""
+    import torch
+    from paper_2602_01723_gb300 import scenes
+    from paper_2602_01723_gb300.sim import Simulator, trajectory
+
+    sc = scenes.WORKLOADS[FB_WORKLOAD]()
+    n, S = sc.n, sc.n_substeps
+    frames = [int(f) for f in sc.frame_sub]
+    sim = Simulator.from_scene(sc)
+    init = {"x": torch.as_tensor(sc.x, device=dev), "v": torch.as_tensor(sc.v, device=dev),
+            "vol": torch.as_tensor(sc.vol, device=dev),
+            "mat_id": torch.as_tensor(sc.mat_id, dtype=torch.int32, device=dev)}
+    with torch.no_grad():
+        target = trajectory(torch.as_tensor(sc.extra["params_true"], device=dev), sim, init, frames).clone()
+    guess = torch.as_tensor(sc.params, device=dev)
+
+    def one_step():
+        params = guess.clone().requires_grad_(True)
+        xs = trajectory(params, sim, init, frames)
+        loss = ((xs - target) ** 2).sum() / (len(frames) * n)
+        loss.backward()
+        return params.grad
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    l0 = sim.stats()["launches"]
+    ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g = one_step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    launches = sim.stats()["launches"] - l0
+    tot = sum(ms)
+    if dist is not None:
+        t = torch.tensor([tot], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
+    value = world * n * S * args.steps / (tot * 1e-3)
+    peak, _ = load_peaks()
+    sim.close()
+    return {"value": value, "unit": UNIT, "workload": FB_WORKLOAD, "particles": n, "grid": sc.grid_res,
+            "substeps_per_step": S, "ckpt_every": sc.ckpt_every, "frames": len(frames),
+            "ms_per_step": tot / args.steps, "bytes_per_particle_substep": FB_BYTES_PER_PS,
+            "hbm_frac": value * FB_BYTES_PER_PS / 1e9 / world / peak, "gpu_launches": int(launches),
+            "grad_finite": bool(torch.isfinite(g).all().item()),
+            "note": "device time of recorded forward + reverse pass, CUDA events; L2 flushed between steps"}
 
 
 def main():

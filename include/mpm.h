@@ -161,6 +161,27 @@ MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream);
  * the record. */
 MPM_API mpm_status mpm_trace(mpm_ctx *ctx, int32_t enable, double ms[3], int64_t count[3]);
 
+/* Segmented sum of a per-particle n x 3 device array (for example the
+ * dL_dparams of mpm_backward) by material id into per_material
+ * (n_materials x 3, device, overwritten): per-object or per-instance
+ * gradients when each object or instance has its own table entry (§4.2: one
+ * parameter set per instance label).  Enqueued on the stream. */
+MPM_API mpm_status mpm_reduce_by_material(mpm_ctx *ctx, const float *per_particle, float *per_material,
+                                          void *stream);
+
+/* Sets the substep kernel's tuning: scatter strategy (0, 1, 2 as in
+ * mpm_options), particles per work chunk (a multiple of 16 in [16, 256]) and
+ * whether steady-state substeps replay a CUDA graph (two substeps per graph
+ * launch; tracing disables the graph). */
+MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, int32_t use_graph);
+
+/* Autotuner: times n_substeps >= 2 substeps from the current state for each
+ * scatter strategy in {1, 2} and chunk size in {64, 128, 256} (each trial
+ * after a warm-up run), keeps the fastest, and restores the state.  out
+ * (nullable, host): chosen scatter, chosen chunk, best time in microseconds.
+ * Synchronises the stream. */
+MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3], void *stream);
+
 /* Diagnostic: P2G of the current state into dense device arrays m
  * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at
  * ((b * R0 + I) * R1 + J) * R2 + K) and mv (3 floats per node); the particle

@@ -56,6 +56,9 @@ SIGNATURES = {
     "mpm_destroy": (ctypes.c_int, [_ctx_p]),
     "mpm_debug_p2g": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     "mpm_trace": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _i64p]),
+    "mpm_reduce_by_material": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+    "mpm_set_tuning": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
+    "mpm_autotune": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, _vp]),
     "mpm_substep_noalloc": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
                                            ctypes.c_int32, ctypes.POINTER(mpm_options), ctypes.c_int64,
                                            _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -160,6 +163,20 @@ def mpm_last_error(ctx):
 def mpm_destroy(ctx):
     if ctx:
         check(lib().mpm_destroy(ctx))
+
+
+def mpm_reduce_by_material(ctx, per_particle, per_material, stream):
+    check(lib().mpm_reduce_by_material(ctx, per_particle, per_material, stream), ctx)
+
+
+def mpm_set_tuning(ctx, scatter, chunk, use_graph):
+    check(lib().mpm_set_tuning(ctx, int(scatter), int(chunk), int(use_graph)), ctx)
+
+
+def mpm_autotune(ctx, n_substeps, stream):
+    out = (ctypes.c_int32 * 3)()
+    check(lib().mpm_autotune(ctx, int(n_substeps), out, stream), ctx)
+    return {"scatter": out[0], "chunk": out[1], "best_us": out[2]}
 
 
 def mpm_debug_p2g(ctx, m, mv, stream):

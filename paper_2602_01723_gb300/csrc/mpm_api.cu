@@ -150,12 +150,8 @@ mpm_status ensure_particles(mpm_ctx *ctx, long long n) {
         ctx->pool_blocks = (unsigned)pool;
     }
     D.max_active = ctx->pool_blocks;
-    unsigned long long chunks = (unsigned long long)(cap / D.chunk) + occ_max + 1;
-    if (chunks > ctx->chunk_cap) {
-        if ((s = dalloc(ctx, &D.chunks, (size_t)chunks, false))) return s;
-        ctx->chunk_cap = (unsigned)chunks;
-    }
-    D.max_chunks = ctx->chunk_cap;
+    if ((s = ensure_chunks(ctx))) return s;
+    ++ctx->generation;
     // staging: inputs are at most 30 floats per particle
     return ensure_stage(ctx, (size_t)cap * 30 * sizeof(float) + 16 * 256);
 }
@@ -163,6 +159,21 @@ mpm_status ensure_particles(mpm_ctx *ctx, long long n) {
 cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 
 }  // namespace
+
+// chunk list large enough for the current chunk size and particle capacity
+mpm_status mpm::ensure_chunks(mpm_ctx *ctx) {
+    Dev &D = ctx->D;
+    unsigned long long occ_max = (unsigned long long)std::min<long long>(ctx->cap, ctx->total_blocks);
+    unsigned long long chunks = (unsigned long long)(ctx->cap / D.chunk) + occ_max + 1;
+    if (chunks > ctx->chunk_cap) {
+        mpm_status s = dalloc(ctx, &D.chunks, (size_t)chunks, false);
+        if (s) return s;
+        ctx->chunk_cap = (unsigned)chunks;
+        ++ctx->generation;
+    }
+    D.max_chunks = ctx->chunk_cap;
+    return MPM_OK;
+}
 
 // ===========================================================================
 // internal sequencing shared with the adjoint translation unit
@@ -200,6 +211,49 @@ void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
     if (ev) cudaEventRecord(ev[1], st);
 }
 
+// one steady-state substep: grid update of buffer par, activation of the
+// other buffer, fused G2P + P2G, plan of the new grouping
+static void middle_substep(mpm_ctx *ctx, int par, cudaStream_t st) {
+    L_grid_update(ctx, par, par ^ 1, st);
+    L_activate_sort(ctx, par ^ 1, 1, st);
+    L_substep(ctx, 1, par, par ^ 1, st);
+    L_plan(ctx, -1, st);
+}
+
+// CUDA graph of two steady-state substeps (parity 0 then 1).  It is captured
+// on a library-owned stream (the legacy default stream cannot be captured)
+// the first time it is needed for this particle count and these buffers, and
+// replayed on the caller's stream.
+static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st) {
+    const long long key = (long long)ctx->D.n * 1000003ll + ctx->generation;
+    if (ctx->graph2 && ctx->graph_key == key) return ctx->graph2;
+    if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
+    cudaStreamCaptureStatus cs;
+    if (st && (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)) {
+        cudaGetLastError();
+        return nullptr;   // the caller is capturing: launch directly into its capture
+    }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cap_stream = nullptr;
+        return nullptr;
+    }
+    const long long l0 = ctx->launches;
+    cudaGraph_t g = nullptr;
+    cudaStream_t cst = ctx->cap_stream;
+    if (cudaStreamBeginCapture(cst, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    middle_substep(ctx, 0, cst);
+    middle_substep(ctx, 1, cst);
+    if (cudaStreamEndCapture(cst, &g) != cudaSuccess || !g) { cudaGetLastError(); ctx->launches = l0; return nullptr; }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) { cudaGetLastError(); ex = nullptr; }
+    cudaGraphDestroy(g);
+    ctx->launches = l0;   // capture launched nothing
+    ctx->graph2 = ex;
+    ctx->graph_key = key;
+    return ex;
+}
+
 // forward of n substeps from the current state (bins must be valid);
 // leaves the state advanced and binned
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
@@ -207,15 +261,26 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
     L_plan(ctx, 0, st);
     L_activate_sort(ctx, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
-    for (int s = 0; s < n_sub; ++s) {
-        int par = s & 1;
-        bool last = s == n_sub - 1;
-        L_grid_update(ctx, par, last ? -1 : (par ^ 1), st);
-        if (!last) {
-            L_activate_sort(ctx, par ^ 1, 1, st);
-            L_substep(ctx, 1, par, par ^ 1, st);
-            L_plan(ctx, -1, st);
+    int s = 0;
+    const int middle = n_sub - 1;
+    if (ctx->use_graph && !ctx->trace_on && middle >= 4) {
+        cudaGraphExec_t ex = graph_pair(ctx, st);
+        if (ex) {
+            for (; s + 1 < middle; s += 2) {
+                if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, MPM_ERR_CUDA, "graph launch failed");
+                }
+                ctx->launches += 8;
+            }
+        }
+    }
+    for (; s < n_sub; ++s) {
+        const int par = s & 1;
+        if (s < middle) {
+            middle_substep(ctx, par, st);
         } else {
+            L_grid_update(ctx, par, -1, st);
             if (s > 0) L_activate_sort(ctx, -1, 1, st);   // sort for the latest plan
             L_substep(ctx, 2, par, 0, st);
         }
@@ -523,7 +588,99 @@ MPM_API mpm_status mpm_destroy(mpm_ctx *ctx) {
     free_adjoint(ctx->adj);
     for (int m = 0; m < 3; ++m)
         for (cudaEvent_t e : ctx->trace_ev[m]) cudaEventDestroy(e);
+    if (ctx->graph2) cudaGraphExecDestroy(ctx->graph2);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     delete ctx;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_reduce_by_material(mpm_ctx *ctx, const float *per_particle, float *per_material, void *stream) {
+    if (!ctx || !per_particle || !per_material) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    if (!is_device_ptr(per_particle) || !is_device_ptr(per_material))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "per_particle and per_material must be device arrays");
+    const int nm = (int)ctx->table.size();
+    if (3 * nm * sizeof(float) > 48 * 1024) return fail(ctx, MPM_ERR_INVALID_ARG, "too many materials for the reduction");
+    cudaStream_t st = S(stream);
+    CK(cudaMemsetAsync(per_material, 0, 3 * nm * sizeof(float), st));
+    launch_reduce_by_material(ctx->D, nm, per_particle, per_material, st);
+    ++ctx->launches;
+    CKLAUNCH();
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, int32_t use_graph) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (scatter < 0 || scatter > 2 || chunk < 16 || chunk > substep_chunk_max() || chunk % 16 != 0)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "scatter in {0,1,2}, chunk a multiple of 16 in [16, 256]");
+    Dev &D = ctx->D;
+    const int old_chunk = D.chunk;
+    D.chunk = chunk;
+    mpm_status s = ensure_chunks(ctx);
+    if (s) { D.chunk = old_chunk; return s; }
+    if (D.scatter != scatter) {
+        D.scatter = scatter;
+        for (int m = 0; m < 3; ++m) {
+            int occ = substep_occupancy(m, D.scatter, ctx->threads);
+            ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
+        }
+    }
+    ctx->use_graph = use_graph != 0;
+    ++ctx->generation;   // kernel arguments changed: recapture
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3], void *stream) {
+    if (!ctx || n_substeps < 2) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state");
+    cudaStream_t st = S(stream);
+    Dev &D = ctx->D;
+    const size_t bytes = (size_t)D.n * REC_F4 * sizeof(float4);
+    // snapshot of the records; the trials run from it and it is restored after
+    float4 *snap = (float4 *)ctx->stage;
+    bool own = false;
+    if (bytes > ctx->stage_bytes) {
+        if (cudaMalloc(&snap, bytes) != cudaSuccess) { cudaGetLastError(); return fail(ctx, MPM_ERR_OOM, "autotune snapshot"); }
+        own = true;
+    }
+    CK(cudaMemcpyAsync(snap, D.rec, bytes, cudaMemcpyDeviceToDevice, st));
+    const int scat0 = D.scatter, chunk0 = D.chunk;
+    const bool graph0 = ctx->use_graph;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bs = scat0, bc = chunk0;
+    const int scats[2] = {1, 2}, chunks[3] = {64, 128, 256};
+    mpm_status s = MPM_OK;
+    for (int a = 0; a < 2 && !s; ++a)
+        for (int b = 0; b < 3 && !s; ++b) {
+            if ((s = mpm_set_tuning(ctx, scats[a], chunks[b], graph0))) break;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && !s; ++rep) {   // first pass warms up (and captures the graph)
+                CK(cudaMemcpyAsync(D.rec, snap, bytes, cudaMemcpyDeviceToDevice, st));
+                L_plan(ctx, -1, st);
+                L_bin(ctx, st);
+                cudaEventRecord(e0, st);
+                s = run_substeps(ctx, n_substeps, st);
+                cudaEventRecord(e1, st);
+                CK(cudaEventSynchronize(e1));
+                cudaEventElapsedTime(&ms, e0, e1);
+            }
+            if (!s && ms < best) { best = ms; bs = scats[a]; bc = chunks[b]; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mpm_status s2 = mpm_set_tuning(ctx, s ? scat0 : bs, s ? chunk0 : bc, graph0);
+    cudaMemcpyAsync(D.rec, snap, bytes, cudaMemcpyDeviceToDevice, st);
+    L_plan(ctx, -1, st);
+    L_bin(ctx, st);
+    mpm_status s3 = check_device_error(ctx, st);
+    if (own) cudaFree(snap);
+    if (s) return s;
+    if (s2) return s2;
+    if (s3) return s3;
+    if (out) { out[0] = D.scatter; out[1] = D.chunk; out[2] = (int32_t)(best * 1000.f); }
     return MPM_OK;
 }
 

@@ -717,6 +717,27 @@ __global__ void k_grid_dense(Dev D, int par, int which, float *m_out, float *mv_
 }
 
 // ---------------------------------------------------------------------------
+// per-material sums of per-particle values (n x 3): shared-memory partial
+// sums per CTA, then one global atomic per material and component
+// ---------------------------------------------------------------------------
+__global__ void k_reduce_by_material(Dev D, int n_mat, const float *__restrict__ vals, float *out) {
+    extern __shared__ float acc[];   // 3 * n_mat
+    for (int t = threadIdx.x; t < 3 * n_mat; t += blockDim.x) acc[t] = 0.f;
+    __syncthreads();
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < D.n; p += gridDim.x * blockDim.x) {
+        const int m = __float_as_int(D.rec[(size_t)p * REC_F4 + 7].y) >> 8;
+        if (m >= 0 && m < n_mat) {
+            atomicAdd(&acc[3 * m], vals[3 * p]);
+            atomicAdd(&acc[3 * m + 1], vals[3 * p + 1]);
+            atomicAdd(&acc[3 * m + 2], vals[3 * p + 2]);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < 3 * n_mat; t += blockDim.x)
+        if (acc[t] != 0.f) atomicAdd(&out[t], acc[t]);
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st) {
@@ -765,5 +786,9 @@ int substep_occupancy(int mode, int scatter, int threads) {
     return scatter == 0 ? occ_of<MODE_FUSED, 0>() : scatter == 1 ? occ_of<MODE_FUSED, 1>() : occ_of<MODE_FUSED, 2>();
 }
 int substep_chunk_max() { return CH_MAX; }
+
+void launch_reduce_by_material(const Dev &D, int n_mat, const float *vals, float *out, cudaStream_t st) {
+    k_reduce_by_material<<<grid_for(D.n, 256, 152 * 4), 256, 3 * n_mat * sizeof(float), st>>>(D, n_mat, vals, out);
+}
 
 }  // namespace mpm

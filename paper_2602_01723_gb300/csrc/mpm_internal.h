@@ -92,6 +92,12 @@ struct mpm_ctx {
     bool trace_on = false;
     std::vector<cudaEvent_t> trace_ev[3];   // per substep mode: start, end, start, end, ...
     size_t trace_used[3] = {0, 0, 0};
+    // CUDA graph of two steady-state substeps (one per grid-buffer parity)
+    bool use_graph = true;
+    cudaStream_t cap_stream = nullptr;   // library-owned stream the graph is captured on
+    cudaGraphExec_t graph2 = nullptr;
+    long long graph_key = -1;     // (n, buffer generation) the graph was captured for
+    long long generation = 0;     // bumped whenever a device buffer the kernels use is reallocated
 };
 
 namespace mpm {
@@ -102,6 +108,8 @@ void L_activate_sort(mpm_ctx *ctx, int par, int do_sort, cudaStream_t st);
 void L_grid_update(mpm_ctx *ctx, int par, int bump_par, cudaStream_t st, int keep_momentum = 0);
 void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
 void L_bin(mpm_ctx *ctx, cudaStream_t st);
+void launch_reduce_by_material(const Dev &D, int n_mat, const float *per_particle, float *out, cudaStream_t st);
+mpm_status ensure_chunks(mpm_ctx *ctx);
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);

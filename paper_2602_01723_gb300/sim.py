@@ -103,6 +103,18 @@ class Simulator:
     def trace(self, enable):
         return L.mpm_trace(self.ctx, enable)
 
+    def reduce_by_material(self, per_particle, stream=None):
+        out = torch.empty((len(self.materials), 3), device=self.device)
+        per_particle = per_particle.contiguous()
+        L.mpm_reduce_by_material(self.ctx, _p(per_particle), _p(out), _stream(stream))
+        return out
+
+    def set_tuning(self, scatter=1, chunk=128, use_graph=True):
+        L.mpm_set_tuning(self.ctx, scatter, chunk, use_graph)
+
+    def autotune(self, n_substeps=20, stream=None):
+        return L.mpm_autotune(self.ctx, n_substeps, _stream(stream))
+
     def record_reset(self):
         L.mpm_record_reset(self.ctx)
 

@@ -1,0 +1,132 @@
+"""GPU tests of the batched form (64 instances, each on its own 64^3 grid),
+the 2M-particle 256^3 block-sparse scene, CUDA-graph replay, the autotuner
+and the per-material gradient reduction."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_01723_gb300 import scenes  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sim_mod():
+    from __graft_entry__ import build
+    build()
+    from paper_2602_01723_gb300 import sim
+    return sim
+
+
+def test_graph_replay_matches_direct_launches(sim_mod):
+    sc = scenes.cube_8k()
+    out = []
+    for g in (False, True):
+        s = sim_mod.Simulator.from_scene(sc)
+        s.set_tuning(1, 128, g)
+        s.load_scene(sc)
+        s.step(50)
+        s.sync()
+        out.append(s.positions().cpu().numpy())
+        s.close()
+    assert np.abs(out[0] - out[1]).max() < 1e-6 * sc.dx
+
+
+def test_autotuner_picks_a_valid_setting_and_restores_the_state(sim_mod):
+    sc = scenes.cube_8k()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    x0 = s.positions().clone()
+    r = s.autotune(10)
+    assert r["scatter"] in (1, 2) and r["chunk"] in (64, 128, 256) and r["best_us"] > 0
+    assert torch.equal(s.positions(), x0)
+    s.step(20)
+    s.sync()
+    s.close()
+
+
+def test_batch_of_64_matches_single_instance_runs(sim_mod):
+    """Instance b of the batch equals the same particles run alone (up to the
+    order of floating-point reductions)."""
+    sc = scenes.batch_64()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(60)
+    s.sync()
+    xb = s.positions().cpu().numpy()
+    st = s.stats()
+    assert st["device_error"] == 0
+    s.close()
+    for b in (0, 17, 63):
+        idx = np.nonzero(sc.instance == b)[0]
+        s1 = sim_mod.Simulator(sc.grid_res, sc.dx, sc.dt, sc.gravity, [sc.materials[b]])
+        s1.load(sc.x[idx], sc.vol[idx], np.zeros(len(idx), np.int32), v=sc.v[idx])
+        s1.step(60)
+        s1.sync()
+        x1 = s1.positions().cpu().numpy()
+        s1.close()
+        assert np.abs(x1 - xb[idx]).max() < 1e-5 * sc.dx, b
+
+
+def test_batch_gradients_per_instance(orc, sim_mod):
+    """Per-instance (log E, nu, yield) gradients of the batched reverse pass:
+    the per-material reduction equals a segmented sum of the per-particle
+    gradients, and instance b's gradient equals the single-instance one.
+    Frames at 70 and 90 substeps: after the floor contact (from substep ~53),
+    where the gradients are physical rather than rounding noise."""
+    sc = scenes.batch_64()
+    frames = [70, 90]
+    rng = np.random.default_rng(1)
+    target = torch.as_tensor(sc.x[None] + 0.005 * rng.standard_normal((2, sc.n, 3)), dtype=torch.float32,
+                             device="cuda")
+    s = sim_mod.Simulator.from_scene(sc)
+    init = {"x": sc.x, "v": sc.v, "vol": sc.vol, "mat_id": sc.mat_id, "instance": sc.instance}
+    params = torch.tensor(np.stack([np.log([m["E"] for m in sc.materials]), [m["nu"] for m in sc.materials],
+                                    [m["yield_stress"] for m in sc.materials]], axis=1)[sc.mat_id],
+                          dtype=torch.float32, device="cuda", requires_grad=True)
+    xs = sim_mod.trajectory(params, s, init, frames)
+    loss = ((xs - target) ** 2).sum()
+    loss.backward()
+    per_inst = s.reduce_by_material(params.grad).cpu().numpy()
+    ref = np.zeros((len(sc.materials), 3))
+    np.add.at(ref, sc.mat_id, params.grad.double().cpu().numpy())
+    assert np.abs(per_inst - ref).max() < 1e-4 * np.abs(ref).max()
+    s.close()
+    b = 5
+    idx = np.nonzero(sc.instance == b)[0]
+    s1 = sim_mod.Simulator(sc.grid_res, sc.dx, sc.dt, sc.gravity, [sc.materials[b]])
+    p1 = params.detach()[idx].clone().requires_grad_(True)
+    xs1 = sim_mod.trajectory(p1, s1, {"x": sc.x[idx], "v": sc.v[idx], "vol": sc.vol[idx],
+                                      "mat_id": np.zeros(len(idx), np.int32)}, frames)
+    ((xs1 - target[:, idx]) ** 2).sum().backward()
+    g1 = p1.grad.double().cpu().numpy().sum(0)
+    assert np.abs(g1 - per_inst[b]).max() < 1e-3 * np.abs(g1).max()
+    s1.close()
+
+
+def test_large_2m_block_sparse_teacher_forced(orc, sim_mod):
+    """2M particles on the 256^3 block-sparse grid: 100 substeps, then one
+    teacher-forced P2G grid against the oracle (dense FP64 grid) and the
+    active-block count against the grid's 262,144 blocks; device memory used."""
+    sc = scenes.large_2m()
+    free0, total = torch.cuda.mem_get_info()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(100)
+    s.sync()
+    free1, _ = torch.cuda.mem_get_info()
+    st = s.stats()
+    assert st["device_error"] == 0
+    assert st["active_blocks"] < 0.2 * (256 // 4) ** 3
+    used_gb = (free0 - free1) / 2 ** 30
+    assert used_gb < 8.0, used_gb
+    stn = {k: t.double().cpu().numpy() for k, t in s.get().items()}
+    m, mv = s.debug_p2g()
+    s.close()
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials)
+    gm, gmv = orc.p2g(cfg, orc.new_state(stn["x"], stn["v"], stn["C"], stn["F"]), mat)
+    floor = np.abs(gm).max() * 9.8 * sc.dt
+    em = np.abs(m[0].double().cpu().numpy() - gm).max() / max(np.abs(gm).max(), floor)
+    emv = np.abs(mv[0].double().cpu().numpy() - gmv).max() / max(np.abs(gmv).max(), floor)
+    assert em < 1e-5 and emv < 1e-5, (em, emv)
