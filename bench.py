@@ -228,11 +228,16 @@ def run_ours(args):
     peak, peak_kind = load_peaks()
     avg_fused_s = fused_ms * 1e-3 / max(fused_n, 1)
     achieved = FWD_BYTES_PER_PS * n / avg_fused_s / 1e9
+    # DRAM bytes per launch from the committed ncu capture, only while the
+    # kernel sources are the ones that capture measured
     traffic = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
+        from paper_2602_01723_gb300.profiling import source_hash
         with open(prof) as f:
-            traffic = json.load(f).get("k_substep_fused_three_objects_300k_bytes_per_launch")
+            t = json.load(f).get("k_substep_fused_three_objects_300k")
+        if t and t.get("source_hash") == source_hash() and t.get("particles") == n:
+            traffic = t["bytes_per_launch"]
 
     # end to end through the C ABI with host (pinned) buffers
     xh = torch.as_tensor(sc.x).pin_memory()
