@@ -91,7 +91,8 @@ typedef struct {
     int64_t max_particles;      /* particle capacity (default 0: set by the first load) */
     int64_t max_active_blocks;  /* capacity of the 4x4x4-node block pool per grid buffer (0: automatic) */
     int32_t ckpt_every;         /* checkpoint interval k of the recorded forward pass (default 20) */
-    int32_t chunk;              /* particles per work item of the substep kernel, <= 256 (0: 128) */
+    int32_t chunk;              /* particles per work item of the substep kernel, <= 128 (0: 128);
+                                   chunks of <= 64 run 64-thread CTAs, larger ones 128-thread CTAs */
     int32_t threads;            /* unused (the substep kernel runs 128-thread CTAs) */
     int32_t scatter;            /* P2G scatter: 0 shared-memory float atomics, 1 int32 fixed-point
                                    shared-memory atomics (default), 2 direct global reductions */
@@ -170,13 +171,13 @@ MPM_API mpm_status mpm_reduce_by_material(mpm_ctx *ctx, const float *per_particl
                                           void *stream);
 
 /* Sets the substep kernel's tuning: scatter strategy (0, 1, 2 as in
- * mpm_options), particles per work chunk (a multiple of 16 in [16, 256]) and
+ * mpm_options), particles per work chunk (a multiple of 16 in [16, 128]) and
  * whether steady-state substeps replay a CUDA graph (two substeps per graph
  * launch; tracing disables the graph). */
 MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, int32_t use_graph);
 
 /* Autotuner: times n_substeps >= 2 substeps from the current state for each
- * scatter strategy in {1, 2} and chunk size in {64, 128, 256} (each trial
+ * scatter strategy in {1, 2} and chunk size in {64, 128} (each trial
  * after a warm-up run), keeps the fastest, and restores the state.  out
  * (nullable, host): chosen scatter, chosen chunk, best time in microseconds.
  * Synchronises the stream. */

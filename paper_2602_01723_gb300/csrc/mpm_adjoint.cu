@@ -639,7 +639,7 @@ static mpm_status dev_alloc(mpm_ctx *ctx, T **p, size_t count) {
 
 // consume any pending binning, then bin the current records
 static void rebin(mpm_ctx *ctx, cudaStream_t st) {
-    L_plan(ctx, -1, st);
+    L_plan(ctx, 0, st);
     L_bin(ctx, st);
 }
 
@@ -650,10 +650,10 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     float4 *saved = D.rec;
     D.rec = state;
     rebin(ctx, st);
-    L_plan(ctx, 0, st);
-    L_activate_sort(ctx, 0, 1, st);
+    L_plan(ctx, 1, st);
+    L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);                       // P2G of the recorded state
-    L_grid_update(ctx, 0, -1, st, 1);                  // v = mask(mv/m + dt g), keeping (mv, m)
+    L_prepare(ctx, 0, -1, 0, st, 1);                   // v = mask(mv/m + dt g), keeping (mv, m)
     const int grid = ctx->grid_sub[1];
     k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);

@@ -180,13 +180,9 @@ mpm_status mpm::ensure_chunks(mpm_ctx *ctx) {
 // ===========================================================================
 namespace mpm {
 
-void L_plan(mpm_ctx *ctx, int bump_par, cudaStream_t st) { launch_plan(ctx->D, bump_par, st); ++ctx->launches; }
-void L_activate_sort(mpm_ctx *ctx, int par, int do_sort, cudaStream_t st) {
-    launch_activate_sort(ctx->D, par, do_sort, ctx->grid_small, st);
-    ++ctx->launches;
-}
-void L_grid_update(mpm_ctx *ctx, int par, int bump_par, cudaStream_t st, int keep_momentum) {
-    launch_grid_update(ctx->D, par, bump_par, ctx->grid_small, st, keep_momentum);
+void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st) { launch_plan(ctx->D, bump_mask, st); ++ctx->launches; }
+void L_prepare(mpm_ctx *ctx, int upd_par, int act_par, int do_sort, cudaStream_t st, int keep_momentum) {
+    launch_prepare(ctx->D, upd_par, act_par, do_sort, keep_momentum, ctx->grid_small, st);
     ++ctx->launches;
 }
 void L_bin(mpm_ctx *ctx, cudaStream_t st) { launch_bin(ctx->D, st); ++ctx->launches; }
@@ -211,13 +207,13 @@ void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
     if (ev) cudaEventRecord(ev[1], st);
 }
 
-// one steady-state substep: grid update of buffer par, activation of the
-// other buffer, fused G2P + P2G, plan of the new grouping
+// one steady-state substep: grid update of buffer par with the activation of
+// the other buffer and the sort, fused G2P + P2G, plan of the new grouping
+// (which opens a fresh epoch for buffer par, activated in the next substep)
 static void middle_substep(mpm_ctx *ctx, int par, cudaStream_t st) {
-    L_grid_update(ctx, par, par ^ 1, st);
-    L_activate_sort(ctx, par ^ 1, 1, st);
+    L_prepare(ctx, par, par ^ 1, 1, st);
     L_substep(ctx, 1, par, par ^ 1, st);
-    L_plan(ctx, -1, st);
+    L_plan(ctx, 1 << par, st);
 }
 
 // CUDA graph of two steady-state substeps (parity 0 then 1).  It is captured
@@ -258,8 +254,8 @@ static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st) {
 // leaves the state advanced and binned
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
     if (n_sub <= 0) return MPM_OK;
-    L_plan(ctx, 0, st);
-    L_activate_sort(ctx, 0, 1, st);
+    L_plan(ctx, 3, st);               // epochs for buffer 0 (P2G below) and 1 (first fused substep)
+    L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
     int s = 0;
     const int middle = n_sub - 1;
@@ -280,8 +276,7 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
         if (s < middle) {
             middle_substep(ctx, par, st);
         } else {
-            L_grid_update(ctx, par, -1, st);
-            if (s > 0) L_activate_sort(ctx, -1, 1, st);   // sort for the latest plan
+            L_prepare(ctx, par, -1, s > 0, st);           // sort for the latest plan
             L_substep(ctx, 2, par, 0, st);
         }
     }
@@ -418,7 +413,7 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     CREATE_TRY(dalloc(ctx, &D.err, 1, true));
     D.scatter = o.scatter;
     for (int m = 0; m < 3; ++m) {
-        int occ = substep_occupancy(m, D.scatter, ctx->threads);
+        int occ = substep_occupancy(m, D.scatter, D.chunk);
         ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->grid_small = ctx->sm_count * 8;
@@ -612,18 +607,16 @@ MPM_API mpm_status mpm_reduce_by_material(mpm_ctx *ctx, const float *per_particl
 MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, int32_t use_graph) {
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (scatter < 0 || scatter > 2 || chunk < 16 || chunk > substep_chunk_max() || chunk % 16 != 0)
-        return fail(ctx, MPM_ERR_INVALID_ARG, "scatter in {0,1,2}, chunk a multiple of 16 in [16, 256]");
+        return fail(ctx, MPM_ERR_INVALID_ARG, "scatter in {0,1,2}, chunk a multiple of 16 in [16, 128]");
     Dev &D = ctx->D;
     const int old_chunk = D.chunk;
     D.chunk = chunk;
     mpm_status s = ensure_chunks(ctx);
     if (s) { D.chunk = old_chunk; return s; }
-    if (D.scatter != scatter) {
-        D.scatter = scatter;
-        for (int m = 0; m < 3; ++m) {
-            int occ = substep_occupancy(m, D.scatter, ctx->threads);
-            ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
-        }
+    D.scatter = scatter;
+    for (int m = 0; m < 3; ++m) {
+        int occ = substep_occupancy(m, D.scatter, D.chunk);
+        ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->use_graph = use_graph != 0;
     ++ctx->generation;   // kernel arguments changed: recapture
@@ -651,15 +644,15 @@ MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3]
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bs = scat0, bc = chunk0;
-    const int scats[2] = {1, 2}, chunks[3] = {64, 128, 256};
+    const int scats[2] = {1, 2}, chunks[2] = {64, 128};
     mpm_status s = MPM_OK;
     for (int a = 0; a < 2 && !s; ++a)
-        for (int b = 0; b < 3 && !s; ++b) {
+        for (int b = 0; b < 2 && !s; ++b) {
             if ((s = mpm_set_tuning(ctx, scats[a], chunks[b], graph0))) break;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && !s; ++rep) {   // first pass warms up (and captures the graph)
                 CK(cudaMemcpyAsync(D.rec, snap, bytes, cudaMemcpyDeviceToDevice, st));
-                L_plan(ctx, -1, st);
+                L_plan(ctx, 0, st);
                 L_bin(ctx, st);
                 cudaEventRecord(e0, st);
                 s = run_substeps(ctx, n_substeps, st);
@@ -673,7 +666,7 @@ MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3]
     cudaEventDestroy(e1);
     mpm_status s2 = mpm_set_tuning(ctx, s ? scat0 : bs, s ? chunk0 : bc, graph0);
     cudaMemcpyAsync(D.rec, snap, bytes, cudaMemcpyDeviceToDevice, st);
-    L_plan(ctx, -1, st);
+    L_plan(ctx, 0, st);
     L_bin(ctx, st);
     mpm_status s3 = check_device_error(ctx, st);
     if (own) cudaFree(snap);
@@ -696,14 +689,14 @@ MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream
     size_t nn = (size_t)ctx->total_blocks * BLK_NODES;
     CK(cudaMemsetAsync(m, 0, nn * sizeof(float), st));
     CK(cudaMemsetAsync(mv, 0, 3 * nn * sizeof(float), st));
-    L_plan(ctx, 0, st);
-    L_activate_sort(ctx, 0, 1, st);
+    L_plan(ctx, 1, st);
+    L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
     launch_grid_dense(D, 0, 0, m, mv, st);
     ++ctx->launches;
     // clear the momentum buffer again (the update zeroes it); the binning of
     // the current positions was consumed by the plan, so rebuild it
-    L_grid_update(ctx, 0, -1, st);
+    L_prepare(ctx, 0, -1, 0, st);
     L_bin(ctx, st);
     CKLAUNCH();
     return check_device_error(ctx, st);

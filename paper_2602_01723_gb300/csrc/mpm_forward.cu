@@ -156,7 +156,7 @@ __device__ __forceinline__ void block_scan2(unsigned a, unsigned b, unsigned &ea
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_par) {
+__global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_mask) {
     __shared__ unsigned sh[66];
     const unsigned n = D.ctr[CTR_N_OCC];
     const unsigned CH = (unsigned)D.chunk;
@@ -189,50 +189,25 @@ __global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_par) {
         D.ctr[CTR_N_PLAN] = n;
         D.ctr[CTR_N_CHUNKS] = min(tchunks, D.max_chunks);
         D.ctr[CTR_N_OCC] = 0;
-        if (bump_par >= 0) {
-            unsigned e = D.ctr[CTR_EPOCH] + 1;
-            D.ctr[CTR_EPOCH] = e;
-            D.ctr[CTR_EPOCH_OF + bump_par] = e;
-            D.ctr[CTR_N_ACTIVE + bump_par] = 0;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// activate the 3x3x3 block neighbourhood of every occupied block in grid
-// buffer `par` (par < 0: no activation), and write the sorted particle index
-// ---------------------------------------------------------------------------
-__global__ void k_activate_sort(Dev D, int par, int do_sort) {
-    const unsigned nplan = D.ctr[CTR_N_PLAN];
-    const unsigned ep = par >= 0 ? D.ctr[CTR_EPOCH_OF + par] : 0u;
-    const unsigned items = par >= 0 ? nplan * 27u : 0u;
-    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    for (unsigned i = tid; i < items; i += stride) {
-        unsigned b = i / 27u, o = i - b * 27u;
-        int inst, bx, by, bz;
-        key_coords(D, D.plan[b], inst, bx, by, bz);
-        int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
-        if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
-        unsigned nk = block_key(D, inst, nx, ny, nz);
-        unsigned old = atomicMax(&D.page_epoch[par][nk], ep);
-        if (old != ep) {
-            unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + par], 1u);
-            if (slot < D.max_active) {
-                D.page[par][nk] = (int)slot;
-                D.active[par][slot] = nk;
-            } else {
-                D.page[par][nk] = -1;
-                set_err(D, ERRB_CAPACITY);
+        // open a fresh activation epoch for each grid buffer in bump_mask
+        for (int par = 0; par < 2; ++par)
+            if (bump_mask & (1 << par)) {
+                const unsigned e = D.ctr[CTR_EPOCH] + 1;
+                D.ctr[CTR_EPOCH] = e;
+                D.ctr[CTR_EPOCH_OF + par] = e;
+                D.ctr[CTR_N_ACTIVE + par] = 0;
             }
-        }
     }
-    if (do_sort)
-        for (unsigned p = tid; p < (unsigned)D.n; p += stride) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
 }
 
 // ---------------------------------------------------------------------------
-// grid update (App. A): v = mv/m + dt g for m > 0, then walls; clears the
-// momentum buffer for its next use
+// one launch between two substep kernels, three independent parts:
+//   * the grid update (App. A) of buffer upd_par: v = mv/m + dt g for m > 0,
+//     then the walls; clears the momentum unless keep_momentum;
+//   * activation in buffer act_par of the 3x3x3 block neighbourhood of every
+//     occupied block of the current grouping (its epoch was opened by k_plan);
+//   * the sorted particle index of the current grouping.
+// upd_par / act_par < 0 skip a part.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void apply_walls(const Dev &D, int I, int J, int K, float &u0, float &u1, float &u2) {
     int idx[3] = {I, J, K};
@@ -251,32 +226,52 @@ __device__ __forceinline__ void apply_walls(const Dev &D, int I, int J, int K, f
     }
 }
 
-__global__ void k_grid_update(Dev D, int par, int bump_par, int keep_momentum) {
-    const unsigned total = D.ctr[CTR_N_ACTIVE + par] * BLK_NODES;
-    if (bump_par >= 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-        // open a fresh epoch for the grid buffer activated next (not read here)
-        unsigned e = D.ctr[CTR_EPOCH] + 1;
-        D.ctr[CTR_EPOCH] = e;
-        D.ctr[CTR_EPOCH_OF + bump_par] = e;
-        D.ctr[CTR_N_ACTIVE + bump_par] = 0;
-    }
-    const unsigned lim = min(total, D.max_active * BLK_NODES);
-    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
-        unsigned slot = i >> 6, l = i & 63u;
-        int inst, bx, by, bz;
-        key_coords(D, D.active[par][slot], inst, bx, by, bz);
-        int I = bx * BLK + (int)(l >> 4), J = by * BLK + (int)((l >> 2) & 3u), K = bz * BLK + (int)(l & 3u);
-        float4 a = D.gmv[par][i];
-        float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (a.w > 0.f) {
-            float im = 1.f / a.w;
-            float u0 = a.x * im + D.dt * D.g[0], u1 = a.y * im + D.dt * D.g[1], u2 = a.z * im + D.dt * D.g[2];
-            apply_walls(D, I, J, K, u0, u1, u2);
-            out = make_float4(u0, u1, u2, a.w);
+__global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep_momentum) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (upd_par >= 0) {
+        const unsigned lim = min(D.ctr[CTR_N_ACTIVE + upd_par], D.max_active) * BLK_NODES;
+        for (unsigned i = tid; i < lim; i += stride) {
+            const unsigned slot = i >> 6, l = i & 63u;
+            int inst, bx, by, bz;
+            key_coords(D, D.active[upd_par][slot], inst, bx, by, bz);
+            const int I = bx * BLK + (int)(l >> 4), J = by * BLK + (int)((l >> 2) & 3u), K = bz * BLK + (int)(l & 3u);
+            const float4 a = D.gmv[upd_par][i];
+            float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.w > 0.f) {
+                const float im = 1.f / a.w;
+                float u0 = a.x * im + D.dt * D.g[0], u1 = a.y * im + D.dt * D.g[1], u2 = a.z * im + D.dt * D.g[2];
+                apply_walls(D, I, J, K, u0, u1, u2);
+                out = make_float4(u0, u1, u2, a.w);
+            }
+            D.gv[upd_par][i] = out;
+            if (!keep_momentum) D.gmv[upd_par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        D.gv[par][i] = out;
-        if (!keep_momentum) D.gmv[par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (act_par >= 0) {
+        const unsigned ep = D.ctr[CTR_EPOCH_OF + act_par];
+        const unsigned items = D.ctr[CTR_N_PLAN] * 27u;
+        for (unsigned i = tid; i < items; i += stride) {
+            const unsigned b = i / 27u, o = i - b * 27u;
+            int inst, bx, by, bz;
+            key_coords(D, D.plan[b], inst, bx, by, bz);
+            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
+            if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
+            const unsigned nk = block_key(D, inst, nx, ny, nz);
+            const unsigned old = atomicMax(&D.page_epoch[act_par][nk], ep);
+            if (old != ep) {
+                const unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + act_par], 1u);
+                if (slot < D.max_active) {
+                    D.page[act_par][nk] = (int)slot;
+                    D.active[act_par][slot] = nk;
+                } else {
+                    D.page[act_par][nk] = -1;
+                    set_err(D, ERRB_CAPACITY);
+                }
+            }
+        }
+    }
+    if (do_sort)
+        for (unsigned p = tid; p < (unsigned)D.n; p += stride) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
 }
 
 // ---------------------------------------------------------------------------
@@ -309,35 +304,43 @@ constexpr int GT = 6;    // gather tile edge (nodes 4B .. 4B+5)
 constexpr int GT3 = GT * GT * GT;
 constexpr int ST = 8;    // scatter tile edge (nodes 4B-1 .. 4B+6)
 constexpr int ST3 = ST * ST * ST;
-constexpr int CH_MAX = 256;   // particles per chunk (records staged in shared memory)
-constexpr int SUB_THREADS = 128;
+constexpr int STP = ST + 1;            // padded row of the fixed-point tile (breaks bank aliasing)
+constexpr int ST3P = ST * ST * STP;
+constexpr int CH_MAX = 128;            // particles per chunk (one per thread)
+__device__ __forceinline__ int tidx(int i, int j, int k) { return (i * ST + j) * STP + k; }
 
 __device__ __forceinline__ int page_slot(const Dev &D, int par, unsigned ep, int inst, int bx, int by, int bz) {
     if (bx < 0 || by < 0 || bz < 0 || bx >= D.NB[0] || by >= D.NB[1] || bz >= D.NB[2]) return -1;
     unsigned k = block_key(D, inst, bx, by, bz);
-    return D.page_epoch[par][k] == ep ? D.page[par][k] : -1;
+    // both words are loaded before either is tested: one round trip
+    const unsigned e = D.page_epoch[par][k];
+    const int sl = D.page[par][k];
+    return e == ep ? sl : -1;
 }
 
 __device__ __forceinline__ int node_local(int I, int J, int K) { return ((I & 3) * 4 + (J & 3)) * 4 + (K & 3); }
 
-struct SubstepSmem {
-    float4 rec[CH_MAX * REC_F4];     // staged records, then scatter packets (4 float4 each)
+constexpr int PK_F4 = 5;          // scatter packet: X(3) m | P(3) - | Ad(9) (+3 spare)
+template <int TPB> struct SubstepSmem {
+    float4 pk[TPB * PK_F4];          // scatter packets of the chunk's particles
     float4 g[GT3];                   // gather tile: (v, m) per node
     union {
-        float f[4 * ST3];            // scatter tile, component-major [m0 | m1 | m2 | m]
-        int i[4 * ST3];
+        float f[4 * ST3P];           // scatter tile, component-major [m0 | m1 | m2 | m], padded rows
+        int i[4 * ST3P];
     } t;
-    unsigned idx[CH_MAX];            // particle index of each chunk slot
     int slot_s[27];                  // pool slot of blocks (B-1 .. B+1)^3 in the scatter grid
     int slot_g[8];                   // pool slot of blocks (B .. B+1)^3 in the gather grid
-    float red[2 * (SUB_THREADS / 32)];
+    float red[2 * (TPB / 32)];
     float scale[2];
 };
 
-template <int MODE, int SCAT>
-__global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int spar) {
+// TPB: threads per CTA = largest chunk (one particle per thread); 64 or 128.
+// Both variants cap registers at 128 (16 warps per SM); the 64-thread one
+// runs twice as many independent CTAs, which overlap each other's staging.
+template <int MODE, int SCAT, int TPB>
+__global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int spar) {
     extern __shared__ float4 smem_raw[];
-    SubstepSmem &S = *reinterpret_cast<SubstepSmem *>(smem_raw);
+    SubstepSmem<TPB> &S = *reinterpret_cast<SubstepSmem<TPB> *>(smem_raw);
     constexpr bool GATHER = MODE != MODE_P2G;
     constexpr bool SCATTER = MODE != MODE_G2P;
     const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
@@ -348,45 +351,67 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
 
     for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const int4 ch = D.chunks[c];
-        const int cnt = min(ch.z, CH_MAX);
+        const int cnt = min(ch.z, TPB);
         int inst, bx, by, bz;
         key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
         const int ox = bx * BLK, oy = by * BLK, oz = bz * BLK;   // gather tile origin (node)
 
-        // ---- 0. staging ---------------------------------------------------
-        for (int j = tid; j < cnt; j += T) S.idx[j] = D.sorted[ch.y + j];
+        // ---- 0. staging: two round trips --------------------------------------
+        // (1) the sorted index of this thread's first particle and the pool
+        //     slots of the tiles' blocks; (2) the particle's record, straight
+        //     into registers (all float4 loads issued together), and the
+        //     gather tile.
+        const int rounds = (cnt + T - 1) / T;
+        unsigned p_next = tid < cnt ? D.sorted[ch.y + tid] : 0u;
         if (SCATTER && tid < 27)
             S.slot_s[tid] = page_slot(D, spar, ep_s, inst, bx + tid / 9 - 1, by + (tid / 3) % 3 - 1, bz + tid % 3 - 1);
         if (GATHER && tid < 8)
             S.slot_g[tid] = page_slot(D, gpar, ep_g, inst, bx + (tid >> 2), by + ((tid >> 1) & 1), bz + (tid & 1));
         if (SCATTER && SCAT != 2)
-            for (int t = tid; t < 4 * ST3; t += T) S.t.i[t] = 0;
+            for (int t = tid; t < 4 * ST3P; t += T) S.t.i[t] = 0;
         __syncthreads();
-        for (int q = tid; q < cnt * REC_F4; q += T) {
-            const int j = q >> 3, w = q & 7;
-            if (GATHER && (w == 2 || w == 3)) continue;   // the old C is not read by G2P
-            S.rec[q] = D.rec[(size_t)S.idx[j] * REC_F4 + w];
+        float4 nr[REC_F4];
+        if (tid < cnt) {
+            const float4 *src = D.rec + (size_t)p_next * REC_F4;
+#pragma unroll
+            for (int w = 0; w < REC_F4; ++w)
+                if (!GATHER || (w != 2 && w != 3)) nr[w] = src[w];   // G2P does not read the old C
         }
-        if (GATHER)
-            for (int t = tid; t < GT3; t += T) {
-                const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
-                const int sl = S.slot_g[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
-                S.g[t] = sl >= 0 ? D.gv[gpar][(size_t)sl * BLK_NODES + node_local(i, j, k)]
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (GATHER) {
+            constexpr int GU = (GT3 + TPB - 1) / TPB;   // tile nodes per thread
+            float4 gt[GU];
+#pragma unroll
+            for (int u = 0; u < GU; ++u) {
+                const int t = tid + u * TPB;
+                gt[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < GT3) {
+                    const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+                    const int sl = S.slot_g[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+                    if (sl >= 0) gt[u] = D.gv[gpar][(size_t)sl * BLK_NODES + node_local(i, j, k)];
+                }
             }
+#pragma unroll
+            for (int u = 0; u < GU; ++u)
+                if (tid + u * TPB < GT3) S.g[tid + u * TPB] = gt[u];
+        }
         __syncthreads();
 
         // ---- A. per-particle update -----------------------------------------
         float bnd_m = 0.f, bnd_v = 0.f;
-        const int rounds = (cnt + T - 1) / T;
         for (int r = 0; r < rounds; ++r) {
             const int j = r * T + tid;
             const bool valid = j < cnt;
             const unsigned lane_mask = __ballot_sync(0xffffffffu, valid);
             if (!valid) continue;
-            const unsigned p = S.idx[j];
-            float4 *sr = S.rec + j * REC_F4;
-            const float4 r0 = sr[0], r1 = sr[1], r6 = sr[6], r7 = sr[7];
+            const unsigned p = r == 0 ? p_next : D.sorted[ch.y + j];
+            if (r > 0) {   // later rounds (chunks larger than the CTA) load here
+                const float4 *src = D.rec + (size_t)p * REC_F4;
+#pragma unroll
+                for (int w = 0; w < REC_F4; ++w)
+                    if (!GATHER || (w != 2 && w != 3)) nr[w] = src[w];
+            }
+            float4 *sr = S.pk + j * PK_F4;
+            const float4 r0 = nr[0], r1 = nr[1], r6 = nr[6], r7 = nr[7];
             float x[3] = {r0.x, r0.y, r0.z};
             const float mass = r0.w, vol = r1.w;
             float v[3] = {r1.x, r1.y, r1.z};
@@ -395,7 +420,7 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
             const int elastic = info & 15, plastic = (info >> 4) & 15;
             float F[9], Cm[9], U[9], s3[3], e3[3];
             {
-                const float4 r4 = sr[4], r5 = sr[5];
+                const float4 r4 = nr[4], r5 = nr[5];
                 F[0] = r4.y; F[1] = r4.z; F[2] = r4.w; F[3] = r5.x; F[4] = r5.y; F[5] = r5.z; F[6] = r5.w;
                 F[7] = r6.x; F[8] = r6.y;
                 Cm[8] = r4.x;
@@ -416,26 +441,35 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                 bspline_w(f0, w0);
                 bspline_w(f1, w1);
                 bspline_w(f2, w2);
+                // separable sums over the 3x3x3 stencil: for each (i, j) the k-sums
+                // S = sum_k w2 g and T = sum_k w2 (k - f2) g, then the j-sums, then
+                // v = sum w g and Bm = sum w g (o - f)^T
                 float vn[3] = {0.f, 0.f, 0.f};
                 float Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                const float wz1[3] = {w2[0] * (0.f - f2), w2[1] * (1.f - f2), w2[2] * (2.f - f2)};
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    const float d0 = (float)i - f0;
+                    float Ui[3] = {0.f, 0.f, 0.f}, Vi[3] = {0.f, 0.f, 0.f}, Wi[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                     for (int jj = 0; jj < 3; ++jj) {
-                        const float d1 = (float)jj - f1;
-                        const float wij = w0[i] * w1[jj];
+                        float Sij[3] = {0.f, 0.f, 0.f}, Tij[3] = {0.f, 0.f, 0.f};
 #pragma unroll
                         for (int k = 0; k < 3; ++k) {
-                            const float d2 = (float)k - f2;
-                            const float wt = wij * w2[k];
                             const float4 g = S.g[((b0 + i) * GT + (b1 + jj)) * GT + (b2 + k)];
-                            const float a0 = wt * g.x, a1 = wt * g.y, a2 = wt * g.z;
-                            vn[0] += a0; vn[1] += a1; vn[2] += a2;
-                            Bm[0] += a0 * d0; Bm[1] += a0 * d1; Bm[2] += a0 * d2;
-                            Bm[3] += a1 * d0; Bm[4] += a1 * d1; Bm[5] += a1 * d2;
-                            Bm[6] += a2 * d0; Bm[7] += a2 * d1; Bm[8] += a2 * d2;
+                            Sij[0] += w2[k] * g.x; Sij[1] += w2[k] * g.y; Sij[2] += w2[k] * g.z;
+                            Tij[0] += wz1[k] * g.x; Tij[1] += wz1[k] * g.y; Tij[2] += wz1[k] * g.z;
                         }
+                        const float wj = w1[jj], wjd = w1[jj] * ((float)jj - f1);
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) { Ui[r] += wj * Sij[r]; Vi[r] += wjd * Sij[r]; Wi[r] += wj * Tij[r]; }
+                    }
+                    const float wi = w0[i], wid = w0[i] * ((float)i - f0);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) {
+                        vn[r] += wi * Ui[r];
+                        Bm[3 * r] += wid * Ui[r];
+                        Bm[3 * r + 1] += wi * Vi[r];
+                        Bm[3 * r + 2] += wi * Wi[r];
                     }
                 }
                 // C = 4/dx^2 sum w v (x_i - x_p)^T with (x_i - x_p) = (o - f) dx
@@ -484,7 +518,7 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                 rp[5] = make_float4(F[3], F[4], F[5], F[6]);
                 rp[6] = make_float4(F[7], F[8], mu, lam);
             } else {
-                const float4 r2 = sr[2], r3 = sr[3];
+                const float4 r2 = nr[2], r3 = nr[3];
                 Cm[0] = r2.x; Cm[1] = r2.y; Cm[2] = r2.z; Cm[3] = r2.w;
                 Cm[4] = r3.x; Cm[5] = r3.y; Cm[6] = r3.z; Cm[7] = r3.w;
                 if (elastic == 0) {
@@ -578,12 +612,12 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                     bnd_m += __shfl_xor_sync(0xffffffffu, bnd_m, o);
                     bnd_v += __shfl_xor_sync(0xffffffffu, bnd_v, o);
                 }
-                if ((tid & 31) == 0) { S.red[tid >> 5] = bnd_m; S.red[(SUB_THREADS / 32) + (tid >> 5)] = bnd_v; }
+                if ((tid & 31) == 0) { S.red[tid >> 5] = bnd_m; S.red[(TPB / 32) + (tid >> 5)] = bnd_v; }
             }
             __syncthreads();
             if (SCAT == 1 && tid == 0) {
                 float bm = 0.f, bv = 0.f;
-                for (int w = 0; w < T / 32; ++w) { bm += S.red[w]; bv += S.red[(SUB_THREADS / 32) + w]; }
+                for (int w = 0; w < T / 32; ++w) { bm += S.red[w]; bv += S.red[(TPB / 32) + w]; }
                 S.scale[0] = bm > 0.f ? 1073741824.f / bm : 1.f;     // 2^30 / bound
                 S.scale[1] = bv > 0.f ? 1073741824.f / bv : 1.f;
             }
@@ -598,11 +632,15 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                 const int u = r * T + tid;
                 const int j = (u & 31) * span + (u >> 5);
                 if (j >= cnt) continue;
-                const float4 q0 = S.rec[j * REC_F4];
+                const float4 q0 = S.pk[j * PK_F4];
                 if (!(q0.w > 0.f)) continue;
-                const float4 q1 = S.rec[j * REC_F4 + 1], q2 = S.rec[j * REC_F4 + 2], q3 = S.rec[j * REC_F4 + 3],
-                             q4 = S.rec[j * REC_F4 + 4];
-                const float Ad[9] = {q2.x, q2.y, q2.z, q2.w, q3.x, q3.y, q3.z, q3.w, q4.x};
+                const float4 q1r = S.pk[j * PK_F4 + 1], q2 = S.pk[j * PK_F4 + 2], q3 = S.pk[j * PK_F4 + 3],
+                             q4 = S.pk[j * PK_F4 + 4];
+                // the fixed-point scale is folded into the packet (1 for SCAT != 1)
+                const float4 q1 = make_float4(q1r.x * sc_v, q1r.y * sc_v, q1r.z * sc_v, 0.f);
+                const float qm = q0.w * sc_m;
+                const float Ad[9] = {q2.x * sc_v, q2.y * sc_v, q2.z * sc_v, q2.w * sc_v, q3.x * sc_v,
+                                     q3.y * sc_v, q3.z * sc_v, q3.w * sc_v, q4.x * sc_v};
                 const float b0f = floorf(q0.x - 0.5f), b1f = floorf(q0.y - 0.5f), b2f = floorf(q0.z - 0.5f);
                 const float f0 = q0.x - b0f, f1 = q0.y - b1f, f2 = q0.z - b2f;
                 const int t0 = (int)b0f, t1 = (int)b1f, t2 = (int)b2f;
@@ -624,18 +662,18 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                             const float d2 = (float)k - f2;
                             const float wt = wij * w2[k];
                             const float m0 = wt * (a0 + Ad[2] * d2), m1 = wt * (a1 + Ad[5] * d2),
-                                        m2 = wt * (a2 + Ad[8] * d2), mm = wt * q0.w;
-                            const int node = ((t0 + i) * ST + (t1 + jj)) * ST + (t2 + k);
+                                        m2 = wt * (a2 + Ad[8] * d2), mm = wt * qm;
+                            const int node = tidx(t0 + i, t1 + jj, t2 + k);
                             if (SCAT == 0) {
                                 atomicAdd(&S.t.f[node], m0);
-                                atomicAdd(&S.t.f[ST3 + node], m1);
-                                atomicAdd(&S.t.f[2 * ST3 + node], m2);
-                                atomicAdd(&S.t.f[3 * ST3 + node], mm);
+                                atomicAdd(&S.t.f[ST3P + node], m1);
+                                atomicAdd(&S.t.f[2 * ST3P + node], m2);
+                                atomicAdd(&S.t.f[3 * ST3P + node], mm);
                             } else if (SCAT == 1) {
-                                atomicAdd(&S.t.i[node], __float2int_rn(m0 * sc_v));
-                                atomicAdd(&S.t.i[ST3 + node], __float2int_rn(m1 * sc_v));
-                                atomicAdd(&S.t.i[2 * ST3 + node], __float2int_rn(m2 * sc_v));
-                                atomicAdd(&S.t.i[3 * ST3 + node], __float2int_rn(mm * sc_m));
+                                atomicAdd(&S.t.i[node], __float2int_rn(m0));
+                                atomicAdd(&S.t.i[ST3P + node], __float2int_rn(m1));
+                                atomicAdd(&S.t.i[2 * ST3P + node], __float2int_rn(m2));
+                                atomicAdd(&S.t.i[3 * ST3P + node], __float2int_rn(mm));
                             } else {
                                 const int I = ox - 1 + t0 + i, J = oy - 1 + t1 + jj, K = oz - 1 + t2 + k;
                                 const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 +
@@ -655,17 +693,18 @@ __global__ void __launch_bounds__(SUB_THREADS, 4) k_substep(Dev D, int gpar, int
                 // flush: one vector reduction per node that received mass
                 const float iv = 1.f / sc_v, im = 1.f / sc_m;
                 for (int t = tid; t < ST3; t += T) {
+                    const int i = t / (ST * ST), j = (t / ST) % ST, k = t % ST;
+                    const int q = tidx(i, j, k);
                     float mm, a0, a1, a2;
                     if (SCAT == 0) {
-                        mm = S.t.f[3 * ST3 + t]; a0 = S.t.f[t]; a1 = S.t.f[ST3 + t]; a2 = S.t.f[2 * ST3 + t];
+                        mm = S.t.f[3 * ST3P + q]; a0 = S.t.f[q]; a1 = S.t.f[ST3P + q]; a2 = S.t.f[2 * ST3P + q];
                     } else {
-                        const int mi = S.t.i[3 * ST3 + t];
+                        const int mi = S.t.i[3 * ST3P + q];
                         mm = (float)mi * im;
                         if (mi == 0) mm = 0.f;
-                        a0 = (float)S.t.i[t] * iv; a1 = (float)S.t.i[ST3 + t] * iv; a2 = (float)S.t.i[2 * ST3 + t] * iv;
+                        a0 = (float)S.t.i[q] * iv; a1 = (float)S.t.i[ST3P + q] * iv; a2 = (float)S.t.i[2 * ST3P + q] * iv;
                     }
                     if (mm != 0.f) {
-                        const int i = t / (ST * ST), j = (t / ST) % ST, k = t % ST;
                         const int I = ox - 1 + i, J = oy - 1 + j, K = oz - 1 + k;
                         const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 + ((K >> 2) - bz + 1)];
                         if (sl >= 0) red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K), a0, a1, a2, mm);
@@ -744,28 +783,30 @@ void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st) {
     k_load<<<grid_for(D.n, 256), 256, 0, st>>>(D, a.x, a.v, a.C, a.F, a.vol, a.mat, a.inst, a.params, a.table);
 }
 void launch_bin(const Dev &D, cudaStream_t st) { k_bin<<<grid_for(D.n, 256), 256, 0, st>>>(D); }
-void launch_plan(const Dev &D, int bump_par, cudaStream_t st) { k_plan<<<1, 1024, 0, st>>>(D, bump_par); }
-void launch_activate_sort(const Dev &D, int par, int do_sort, int grid, cudaStream_t st) {
-    k_activate_sort<<<grid, 256, 0, st>>>(D, par, do_sort);
+void launch_plan(const Dev &D, int bump_mask, cudaStream_t st) { k_plan<<<1, 1024, 0, st>>>(D, bump_mask); }
+void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st) {
+    k_prepare<<<grid, 256, 0, st>>>(D, upd_par, act_par, do_sort, keep_momentum);
 }
-void launch_grid_update(const Dev &D, int par, int bump_par, int grid, cudaStream_t st, int keep_momentum) {
-    k_grid_update<<<grid, 256, 0, st>>>(D, par, bump_par, keep_momentum);
+template <int MODE, int SCAT, int TPB> static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
+    k_substep<MODE, SCAT, TPB><<<grid, TPB, sizeof(SubstepSmem<TPB>), st>>>(D, gpar, spar);
 }
-template <int MODE, int SCAT> static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
-    k_substep<MODE, SCAT><<<grid, SUB_THREADS, sizeof(SubstepSmem), st>>>(D, gpar, spar);
-}
-void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st) {
-    (void)threads;
-    if (mode == MODE_G2P) { launch_sub<MODE_G2P, 2>(D, gpar, spar, grid, st); return; }
+template <int TPB> static void launch_tpb(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st) {
+    if (mode == MODE_G2P) { launch_sub<MODE_G2P, 2, TPB>(D, gpar, spar, grid, st); return; }
     if (mode == MODE_P2G) {
-        if (D.scatter == 0) launch_sub<MODE_P2G, 0>(D, gpar, spar, grid, st);
-        else if (D.scatter == 1) launch_sub<MODE_P2G, 1>(D, gpar, spar, grid, st);
-        else launch_sub<MODE_P2G, 2>(D, gpar, spar, grid, st);
+        if (D.scatter == 0) launch_sub<MODE_P2G, 0, TPB>(D, gpar, spar, grid, st);
+        else if (D.scatter == 1) launch_sub<MODE_P2G, 1, TPB>(D, gpar, spar, grid, st);
+        else launch_sub<MODE_P2G, 2, TPB>(D, gpar, spar, grid, st);
         return;
     }
-    if (D.scatter == 0) launch_sub<MODE_FUSED, 0>(D, gpar, spar, grid, st);
-    else if (D.scatter == 1) launch_sub<MODE_FUSED, 1>(D, gpar, spar, grid, st);
-    else launch_sub<MODE_FUSED, 2>(D, gpar, spar, grid, st);
+    if (D.scatter == 0) launch_sub<MODE_FUSED, 0, TPB>(D, gpar, spar, grid, st);
+    else if (D.scatter == 1) launch_sub<MODE_FUSED, 1, TPB>(D, gpar, spar, grid, st);
+    else launch_sub<MODE_FUSED, 2, TPB>(D, gpar, spar, grid, st);
+}
+// the chunk size selects the CTA size: chunks of <= 64 particles run 64-thread CTAs
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st) {
+    (void)threads;
+    if (D.chunk <= 64) launch_tpb<64>(D, mode, gpar, spar, grid, st);
+    else launch_tpb<128>(D, mode, gpar, spar, grid, st);
 }
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st) {
     k_export<<<grid_for(D.n, 256), 256, 0, st>>>(D, x, v, C, F);
@@ -773,17 +814,22 @@ void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStr
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st) {
     k_grid_dense<<<1024, 256, 0, st>>>(D, par, which, m, mv);
 }
-template <int MODE, int SCAT> static int occ_of() {
+template <int MODE, int SCAT, int TPB> static int occ_of() {
     int nb = 0;
-    cudaFuncSetAttribute(k_substep<MODE, SCAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SubstepSmem));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT>, SUB_THREADS, sizeof(SubstepSmem));
+    cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(SubstepSmem<TPB>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT, TPB>, TPB, sizeof(SubstepSmem<TPB>));
     return nb;
 }
-int substep_occupancy(int mode, int scatter, int threads) {
-    (void)threads;
-    if (mode == MODE_G2P) return occ_of<MODE_G2P, 2>();
-    if (mode == MODE_P2G) return scatter == 0 ? occ_of<MODE_P2G, 0>() : scatter == 1 ? occ_of<MODE_P2G, 1>() : occ_of<MODE_P2G, 2>();
-    return scatter == 0 ? occ_of<MODE_FUSED, 0>() : scatter == 1 ? occ_of<MODE_FUSED, 1>() : occ_of<MODE_FUSED, 2>();
+template <int TPB> static int occ_tpb(int mode, int scatter) {
+    if (mode == MODE_G2P) return occ_of<MODE_G2P, 2, TPB>();
+    if (mode == MODE_P2G)
+        return scatter == 0 ? occ_of<MODE_P2G, 0, TPB>() : scatter == 1 ? occ_of<MODE_P2G, 1, TPB>() : occ_of<MODE_P2G, 2, TPB>();
+    return scatter == 0 ? occ_of<MODE_FUSED, 0, TPB>() : scatter == 1 ? occ_of<MODE_FUSED, 1, TPB>() : occ_of<MODE_FUSED, 2, TPB>();
+}
+// resident CTAs per SM of the substep kernel for a mode, scatter strategy and chunk size
+int substep_occupancy(int mode, int scatter, int chunk) {
+    return chunk <= 64 ? occ_tpb<64>(mode, scatter) : occ_tpb<128>(mode, scatter);
 }
 int substep_chunk_max() { return CH_MAX; }
 

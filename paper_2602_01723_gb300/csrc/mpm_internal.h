@@ -33,13 +33,12 @@ inline int grid_for(long long n, int threads, int cap = 152 * 16) {
 
 void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st);
 void launch_bin(const Dev &D, cudaStream_t st);
-void launch_plan(const Dev &D, int par_next, cudaStream_t st);
-void launch_activate_sort(const Dev &D, int par, int do_sort, int grid, cudaStream_t st);
-void launch_grid_update(const Dev &D, int par, int bump_par, int grid, cudaStream_t st, int keep_momentum = 0);
+void launch_plan(const Dev &D, int bump_mask, cudaStream_t st);
+void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st);
 void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st);
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st);
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
-int substep_occupancy(int mode, int scatter, int threads);
+int substep_occupancy(int mode, int scatter, int chunk);
 int substep_chunk_max();
 
 // recorded trajectory and reverse-pass buffers
@@ -103,9 +102,10 @@ struct mpm_ctx {
 namespace mpm {
 // kernel launches through these wrappers are counted (and the substep kernel
 // timed when tracing is on)
-void L_plan(mpm_ctx *ctx, int bump_par, cudaStream_t st);
-void L_activate_sort(mpm_ctx *ctx, int par, int do_sort, cudaStream_t st);
-void L_grid_update(mpm_ctx *ctx, int par, int bump_par, cudaStream_t st, int keep_momentum = 0);
+// plan of the current grouping; opens fresh epochs for the buffers in bump_mask
+void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st);
+// grid update of upd_par, activation of act_par, sorted index (see k_prepare)
+void L_prepare(mpm_ctx *ctx, int upd_par, int act_par, int do_sort, cudaStream_t st, int keep_momentum = 0);
 void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
 void L_bin(mpm_ctx *ctx, cudaStream_t st);
 void launch_reduce_by_material(const Dev &D, int n_mat, const float *per_particle, float *out, cudaStream_t st);

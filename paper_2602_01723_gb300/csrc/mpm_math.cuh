@@ -33,6 +33,14 @@ __device__ __forceinline__ double t_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float t_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double t_abs(double x) { return fabs(x); }
 
+// reciprocal and reciprocal square root: the MUFU approximations in FP32
+// (relative error of a few ulp, enough wherever a quantity is normalised or
+// only its relative precision matters), exact IEEE operations in FP64
+__device__ __forceinline__ float t_rcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double t_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float t_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double t_rsqrt(double x) { return 1.0 / sqrt(x); }
+
 template <typename T> struct Tol;
 template <> struct Tol<float> {
     static constexpr float rank = 1e-3f;     // sigma_2/sigma_0 below this goes to the FP64 branch
@@ -72,9 +80,9 @@ __device__ __forceinline__ void bspline_dw(float fx, float dw[3]) {   // d w / d
 //
 // Eigen-decomposition of D = F^T F - I, formed from H = F - I as
 // H + H^T + H^T H so that small strains keep their relative precision:
-//  * eigenvalues of the deviatoric part by the trigonometric solution of the
-//    depressed characteristic cubic y^3 - 3y = 2r (Smith 1961), the most
-//    isolated root then polished by Newton steps on that cubic;
+//  * the deviatoric part scaled to the depressed characteristic cubic
+//    y^3 - 3y = 2r (Smith 1961), whose most isolated root is found by Newton
+//    iteration from an analytic start;
 //  * its eigenvector as the largest cross product of two rows of the shifted
 //    matrix (Kopp 2008);
 //  * the remaining pair by one exact 2x2 Jacobi rotation in the orthogonal
@@ -103,9 +111,9 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
             D[3 * i + j] = v;
             D[3 * j + i] = v;
         }
-    T q = (D[0] + D[4] + D[8]) / T(3);
+    T q = (D[0] + D[4] + D[8]) * T(1.0 / 3.0);
     T b00 = D[0] - q, b11 = D[4] - q, b22 = D[8] - q, b01 = D[1], b02 = D[2], b12 = D[5];
-    T p2 = (b00 * b00 + b11 * b11 + b22 * b22 + T(2) * (b01 * b01 + b02 * b02 + b12 * b12)) / T(6);
+    T p2 = (b00 * b00 + b11 * b11 + b22 * b22 + T(2) * (b01 * b01 + b02 * b02 + b12 * b12)) * T(1.0 / 6.0);
     T y[3];
     T vv[3][3];   // eigenvectors (as rows here; transposed into V below)
     if (!(p2 > T(0))) {
@@ -116,22 +124,21 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         vv[2][0] = T(0); vv[2][1] = T(0); vv[2][2] = T(1);
         p2 = T(0);
     } else {
-        T p = t_sqrt(p2), ip = T(1) / p;
+        T p = t_sqrt(p2), ip = t_rcp(p);
         T c00 = b00 * ip, c11 = b11 * ip, c22 = b22 * ip, c01 = b01 * ip, c02 = b02 * ip, c12 = b12 * ip;
         T r = T(0.5) * (c00 * (c11 * c22 - c12 * c12) - c01 * (c01 * c22 - c12 * c02) + c02 * (c01 * c12 - c11 * c02));
         r = r > T(1) ? T(1) : (r < T(-1) ? T(-1) : r);
-        T phi = t_acos(r) / T(3);
-        T y0 = T(2) * t_cos(phi);
-        T y2 = T(2) * t_cos(phi + T(2.0943951023931954923));   // + 2 pi / 3
-        T y1 = -y0 - y2;
-        // the most isolated root; polish it on y^3 - 3y - 2r = 0
-        bool top = (y0 - y1) >= (y1 - y2);
-        T yi = top ? y0 : y2;
+        // The roots of y^3 - 3y - 2r = 0 lie in [-2, 2].  For r >= 0 the
+        // largest one (in [sqrt3, 2]) is the most isolated, for r < 0 the
+        // smallest.  Newton from +-2, whose first step is taken analytically;
+        // f' = 3y^2 - 3 >= 6 on that interval, and the error squares each step
+        // (4e-2, 2e-3, 3e-6, 1e-11 for the worst case r = 0).
+        const T sg = r >= T(0) ? T(1) : T(-1);
+        T yi = sg * (T(2) - (T(2) - T(2) * sg * r) * T(1.0 / 9.0));
 #pragma unroll
-        for (int it = 0; it < 2; ++it) {
-            T f = yi * yi * yi - T(3) * yi - T(2) * r;
-            T fp = T(3) * yi * yi - T(3);
-            if (t_abs(fp) > T(1e-3)) yi -= f / fp;
+        for (int it = 0; it < 3; ++it) {
+            const T y2 = yi * yi;
+            yi -= (y2 * yi - T(3) * yi - T(2) * r) * t_rcp(T(3) * y2 - T(3));
         }
         // eigenvector of the isolated root: null vector of C - yi I
         T m0[3] = {c00 - yi, c01, c02}, m1[3] = {c01, c11 - yi, c12}, m2[3] = {c02, c12, c22 - yi};
@@ -146,7 +153,7 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         if (n02 > nbest) { nbest = n02; vi[0] = x02[0]; vi[1] = x02[1]; vi[2] = x02[2]; }
         if (n12 > nbest) { nbest = n12; vi[0] = x12[0]; vi[1] = x12[1]; vi[2] = x12[2]; }
         if (!(nbest > Tol<T>::tiny)) return false;
-        T inv = T(1) / t_sqrt(nbest);
+        T inv = t_rsqrt(nbest);
         vi[0] *= inv; vi[1] *= inv; vi[2] *= inv;
         // orthonormal basis (e1, e2) of the complement
         T ax[3] = {T(0), T(0), T(0)};
@@ -156,7 +163,7 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         else ax[2] = T(1);
         T e1[3], e2[3];
         cross3(e1, vi, ax);
-        T ne = T(1) / t_sqrt(dot3(e1, e1));
+        T ne = t_rsqrt(dot3(e1, e1));
         e1[0] *= ne; e1[1] *= ne; e1[2] *= ne;
         cross3(e2, vi, e1);
         // 2x2 block of C in that basis
@@ -167,9 +174,9 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         T aa = dot3(e1, Ce1), bb = dot3(e1, Ce2), cc = dot3(e2, Ce2);
         T cs = T(1), sn = T(0), tj = T(0);
         if (bb != T(0)) {
-            T th = (cc - aa) / (T(2) * bb);
-            tj = (th >= T(0) ? T(1) : T(-1)) / (t_abs(th) + t_sqrt(th * th + T(1)));
-            cs = T(1) / t_sqrt(tj * tj + T(1));
+            T th = (cc - aa) * t_rcp(T(2) * bb);
+            tj = (th >= T(0) ? T(1) : T(-1)) * t_rcp(t_abs(th) + t_sqrt(th * th + T(1)));
+            cs = t_rsqrt(tj * tj + T(1));
             sn = tj * cs;
         }
         T ya = aa - tj * bb, yb = cc + tj * bb;
@@ -210,7 +217,7 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
     }
     T n0 = dot3(f0, f0);
     if (!(n0 > Tol<T>::tiny)) return false;
-    T in0 = T(1) / t_sqrt(n0);
+    T in0 = t_rsqrt(n0);
     T u0[3] = {f0[0] * in0, f0[1] * in0, f0[2] * in0};
     T pr = dot3(u0, f1);
     T g1[3] = {f1[0] - pr * u0[0], f1[1] - pr * u0[1], f1[2] - pr * u0[2]};
@@ -225,10 +232,10 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         else if (a1 <= a2) ax[1] = T(1);
         else ax[2] = T(1);
         cross3(u1, u0, ax);
-        T nn = T(1) / t_sqrt(dot3(u1, u1));
+        T nn = t_rsqrt(dot3(u1, u1));
         u1[0] *= nn; u1[1] *= nn; u1[2] *= nn;
     } else {
-        T in1 = T(1) / t_sqrt(n1);
+        T in1 = t_rsqrt(n1);
         u1[0] = g1[0] * in1; u1[1] = g1[1] * in1; u1[2] = g1[2] * in1;
     }
     T u2[3];
@@ -242,14 +249,14 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
         T sq = T(1) + d[k];
         if (!(sq > T(0))) return false;
         s[k] = t_sqrt(sq);
-        e[k] = d[k] / (T(1) + s[k]);
+        e[k] = d[k] * t_rcp(T(1) + s[k]);
     }
     {
         T sq = T(1) + d[2];
         sq = sq > T(0) ? sq : T(0);
         T m = t_sqrt(sq);
         if (Tol<T>::rank > T(0) && !(m > Tol<T>::rank * s[0])) return false;
-        if (s2sign >= T(0)) { s[2] = m; e[2] = d[2] / (T(1) + m); }
+        if (s2sign >= T(0)) { s[2] = m; e[2] = d[2] * t_rcp(T(1) + m); }
         else { s[2] = -m; e[2] = -m - T(1); }
     }
     return true;
