@@ -257,54 +257,109 @@ struct ParticleIn {
     float mass, vol, mu, lam, yield, alpha;
     int elastic, plastic;
 };
-__device__ __forceinline__ void load_particle(const float4 *r, ParticleIn &P) {
-    const float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6], r7 = r[7];
-    P.x[0] = r0.x; P.x[1] = r0.y; P.x[2] = r0.z; P.mass = r0.w;
-    P.v[0] = r1.x; P.v[1] = r1.y; P.v[2] = r1.z; P.vol = r1.w;
-    P.C[0] = r2.x; P.C[1] = r2.y; P.C[2] = r2.z; P.C[3] = r2.w;
-    P.C[4] = r3.x; P.C[5] = r3.y; P.C[6] = r3.z; P.C[7] = r3.w; P.C[8] = r4.x;
-    P.F[0] = r4.y; P.F[1] = r4.z; P.F[2] = r4.w; P.F[3] = r5.x; P.F[4] = r5.y; P.F[5] = r5.z; P.F[6] = r5.w;
-    P.F[7] = r6.x; P.F[8] = r6.y;
-    P.mu = r6.z; P.lam = r6.w; P.yield = r7.x;
-    const int info = __float_as_int(r7.y);
+__device__ __forceinline__ void unpack_particle(const float4 r[REC_F4], ParticleIn &P) {
+    P.x[0] = r[0].x; P.x[1] = r[0].y; P.x[2] = r[0].z; P.mass = r[0].w;
+    P.v[0] = r[1].x; P.v[1] = r[1].y; P.v[2] = r[1].z; P.vol = r[1].w;
+    P.C[0] = r[2].x; P.C[1] = r[2].y; P.C[2] = r[2].z; P.C[3] = r[2].w;
+    P.C[4] = r[3].x; P.C[5] = r[3].y; P.C[6] = r[3].z; P.C[7] = r[3].w; P.C[8] = r[4].x;
+    P.F[0] = r[4].y; P.F[1] = r[4].z; P.F[2] = r[4].w; P.F[3] = r[5].x; P.F[4] = r[5].y; P.F[5] = r[5].z;
+    P.F[6] = r[5].w; P.F[7] = r[6].x; P.F[8] = r[6].y;
+    P.mu = r[6].z; P.lam = r[6].w; P.yield = r[7].x;
+    const int info = __float_as_int(r[7].y);
     P.elastic = info & 15;
     P.plastic = (info >> 4) & 15;
-    P.alpha = r7.w;
+    P.alpha = r[7].w;
 }
 
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
+// shared memory of the reverse G2P kernel
+constexpr int GTP = GT + 1;                  // padded row of the fixed-point tile
+constexpr int GT3P = GT * GT * GTP;
+__device__ __forceinline__ int gidx(int i, int j, int k) { return (i * GT + j) * GTP + k; }
+struct AdjG2PSmem {
+    float4 g[GT3];                           // grid velocity tile (v, m)
+    int t[3 * GT3P];                         // fixed-point grid-velocity adjoint, component-major
+    float4 pk[ADJ_THREADS * 4];              // packets: f(3) - | vt(3) - | Ct(9) ...
+    int slot[8];
+    float red[ADJ_THREADS / 32];
+    float scale;
+};
+
+// Reverse of G2P, advection, F update and return map for the particles of
+// one chunk per iteration.  Phase A (one particle per thread, record and
+// adjoint loaded into registers after one round trip for the sorted index):
+// recompute v', C', G = (I + dt C') F; reverse the return map, the F update
+// and advection; accumulate the position adjoint of the gathers; leave a
+// packet (position in the tile, vbar_tot, Cbar_tot).  Phase B: scatter the
+// grid-velocity adjoint wt (vbar_tot + 4/dx^2 Cbar_tot (x_i - x_p)) into an
+// int32 fixed-point tile (per-chunk scale 2^30 / sum of per-particle bounds)
+// and flush it with one vector reduction per touched node.
+__global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
                                                          float4 *gpar, float4 *gbar) {
-    __shared__ float4 s_g[GT3];
-    __shared__ int s_slot[8];
+    __shared__ AdjG2PSmem S;
     const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
     const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
     const float c4 = 4.f * inv_dx * inv_dx;
+    const int tid = threadIdx.x;
     for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
         const int4 ch = D.chunks[c];
+        const int cnt = min(ch.z, ADJ_THREADS);
         int inst, bx, by, bz;
         key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
-        load_tile(D, D.gv[0], ep, inst, bx, by, bz, s_g, s_slot);
-        for (int j = threadIdx.x; j < ch.z; j += blockDim.x) {
-            const unsigned p = D.sorted[ch.y + j];
+        const bool valid = tid < cnt;
+        const unsigned p = valid ? D.sorted[ch.y + tid] : 0u;
+        if (tid < 8) S.slot[tid] = page_slot_a(D, 0, ep, inst, bx + (tid >> 2), by + ((tid >> 1) & 1), bz + (tid & 1));
+        for (int t = tid; t < 3 * GT3P; t += ADJ_THREADS) S.t[t] = 0;
+        __syncthreads();
+        float4 rr[REC_F4], aa[ADJ_F4];
+        if (valid) {
+#pragma unroll
+            for (int w = 0; w < REC_F4; ++w) if (w != 2 && w != 3) rr[w] = D.rec[(size_t)p * REC_F4 + w];
+#pragma unroll
+            for (int w = 0; w < ADJ_F4; ++w) aa[w] = ain[(size_t)p * ADJ_F4 + w];
+        }
+        {
+            float4 gt[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int t = tid + u * ADJ_THREADS;
+                gt[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (t < GT3) {
+                    const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+                    const int sl = S.slot[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+                    if (sl >= 0) gt[u] = D.gv[0][(size_t)sl * BLK_NODES + node_loc(i, j, k)];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (tid + u * ADJ_THREADS < GT3) S.g[tid + u * ADJ_THREADS] = gt[u];
+        }
+        __syncthreads();
+        float bnd = 0.f;
+        if (valid) {
+            rr[2] = rr[3] = make_float4(0.f, 0.f, 0.f, 0.f);
             ParticleIn P;
-            load_particle(D.rec + (size_t)p * REC_F4, P);
+            unpack_particle(rr, P);
             float f[3];
             int b[3];
             b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
             b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
             b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
-            if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); continue; }
+            const bool ok = (unsigned)b[0] <= 3u && (unsigned)b[1] <= 3u && (unsigned)b[2] <= 3u;
+            if (!ok) { set_err(D, ERRB_CFL); b[0] = min(max(b[0], 0), 3); b[1] = min(max(b[1], 0), 3); b[2] = min(max(b[2], 0), 3); }
             float w[3][3], dw[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
             // recompute v' and C'
             float vn[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
             for (int i = 0; i < 3; ++i)
+#pragma unroll
                 for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const float wt = w[0][i] * w[1][jj] * w[2][k];
-                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
                         const float dd[3] = {(float)i - f[0], (float)jj - f[1], (float)k - f[2]};
                         const float a3[3] = {wt * g.x, wt * g.y, wt * g.z};
 #pragma unroll
@@ -324,12 +379,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_g2p(Dev D, const float4 *__
                     G[3 * r + cc] = P.F[3 * r + cc] + dt * (Cn[3 * r] * P.F[cc] + Cn[3 * r + 1] * P.F[3 + cc] +
                                                             Cn[3 * r + 2] * P.F[6 + cc]);
             // adjoint of the new state
-            const float4 *ap = ain + (size_t)p * ADJ_F4;
-            const float4 a0 = ap[0], a1 = ap[1], a2 = ap[2], a3v = ap[3], a4 = ap[4], a5 = ap[5];
-            const float xb[3] = {a0.x, a0.y, a0.z};
-            const float vb[3] = {a0.w, a1.x, a1.y};
-            const float Cb[9] = {a1.z, a1.w, a2.x, a2.y, a2.z, a2.w, a3v.x, a3v.y, a3v.z};
-            const float Fb[9] = {a3v.w, a4.x, a4.y, a4.z, a4.w, a5.x, a5.y, a5.z, a5.w};
+            const float xb[3] = {aa[0].x, aa[0].y, aa[0].z};
+            const float vb[3] = {aa[0].w, aa[1].x, aa[1].y};
+            const float Cb[9] = {aa[1].z, aa[1].w, aa[2].x, aa[2].y, aa[2].z, aa[2].w, aa[3].x, aa[3].y, aa[3].z};
+            const float Fb[9] = {aa[3].w, aa[4].x, aa[4].y, aa[4].z, aa[4].w, aa[5].x, aa[5].y, aa[5].z, aa[5].w};
             // reverse of the return map
             float Gb[9];
 #pragma unroll
@@ -356,33 +409,30 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_g2p(Dev D, const float4 *__
             // x' = x + dt v'
             float xa[3] = {xb[0], xb[1], xb[2]};
             const float vt[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
-            // reverse of the gathers
+            // reverse of the gathers: position adjoint through the weights and x_i - x_p
+#pragma unroll 1
             for (int i = 0; i < 3; ++i)
+#pragma unroll
                 for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
                         const float wt = w[0][i] * w[1][jj] * w[2][k];
                         const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
                                              w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
                         const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
-                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
                         const float vi[3] = {g.x, g.y, g.z};
-                        float cd[3], wbar = 0.f;
+                        float wbar = 0.f;
 #pragma unroll
                         for (int r = 0; r < 3; ++r) {
-                            cd[r] = Ct[3 * r] * dp[0] + Ct[3 * r + 1] * dp[1] + Ct[3 * r + 2] * dp[2];
-                            wbar += vt[r] * vi[r] + c4 * vi[r] * cd[r];
+                            const float cd = Ct[3 * r] * dp[0] + Ct[3 * r + 1] * dp[1] + Ct[3 * r + 2] * dp[2];
+                            wbar += vt[r] * vi[r] + c4 * vi[r] * cd;
                         }
 #pragma unroll
                         for (int cc = 0; cc < 3; ++cc) {
                             const float dpb = c4 * wt * (Ct[cc] * vi[0] + Ct[3 + cc] * vi[1] + Ct[6 + cc] * vi[2]);
                             xa[cc] += wbar * gw[cc] - dpb;
                         }
-                        const int sl = s_slot[(((b[0] + i) >> 2) << 2) | (((b[1] + jj) >> 2) << 1) | ((b[2] + k) >> 2)];
-                        if (sl >= 0)
-                            red_add_v4(gbar + (size_t)sl * BLK_NODES + node_loc(b[0] + i, b[1] + jj, b[2] + k),
-                                       wt * (vt[0] + c4 * cd[0]), wt * (vt[1] + c4 * cd[1]), wt * (vt[2] + c4 * cd[2]), 0.f);
-                        else
-                            set_err(D, ERRB_CAPACITY);
                     }
             float4 *op = aout + (size_t)p * ADJ_F4;
             op[0] = make_float4(xa[0], xa[1], xa[2], 0.f);
@@ -396,6 +446,77 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_g2p(Dev D, const float4 *__
             float4 g4 = gpar[p];
             g4.x += gE; g4.y += gnu; g4.z += ybar;
             gpar[p] = g4;
+            // packet for the scatter of the grid-velocity adjoint
+            // base cell (0..3 per axis) exactly in .w as 1 + b0 + 4 b1 + 16 b2 (> 0 marks a valid packet)
+            S.pk[tid * 4 + 0] = make_float4(f[0], f[1], f[2], (float)(1 + b[0] + 4 * b[1] + 16 * b[2]));
+            S.pk[tid * 4 + 1] = make_float4(vt[0], vt[1], vt[2], Ct[0]);
+            S.pk[tid * 4 + 2] = make_float4(Ct[1], Ct[2], Ct[3], Ct[4]);
+            S.pk[tid * 4 + 3] = make_float4(Ct[5], Ct[6], Ct[7], Ct[8]);
+            float cm = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) cm = fmaxf(cm, fabsf(Ct[t]));
+            bnd = fmaxf(fabsf(vt[0]), fmaxf(fabsf(vt[1]), fabsf(vt[2]))) + 4.5f * c4 * dx * cm;
+        } else {
+            S.pk[tid * 4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        // per-chunk fixed-point scale
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
+        if ((tid & 31) == 0) S.red[tid >> 5] = bnd;
+        __syncthreads();
+        if (tid == 0) {
+            float bs = 0.f;
+            for (int wq = 0; wq < ADJ_THREADS / 32; ++wq) bs += S.red[wq];
+            S.scale = bs > 0.f ? 1073741824.f / bs : 1.f;
+        }
+        __syncthreads();
+        const float sc = S.scale;
+        // phase B: lane-transposed mapping spreads a warp over the chunk's cells
+        {
+            const int j = (tid & 31) * (ADJ_THREADS / 32) + (tid >> 5);
+            const float4 q0 = S.pk[j * 4];
+            if (j < cnt && q0.w > 0.f) {
+                const float4 q1 = S.pk[j * 4 + 1], q2 = S.pk[j * 4 + 2], q3 = S.pk[j * 4 + 3];
+                const float vt[3] = {q1.x * sc, q1.y * sc, q1.z * sc};
+                const float Cs[9] = {q1.w * sc * c4 * dx, q2.x * sc * c4 * dx, q2.y * sc * c4 * dx,
+                                     q2.z * sc * c4 * dx, q2.w * sc * c4 * dx, q3.x * sc * c4 * dx,
+                                     q3.y * sc * c4 * dx, q3.z * sc * c4 * dx, q3.w * sc * c4 * dx};
+                const int code = (int)q0.w - 1;
+                const int b[3] = {code & 3, (code >> 2) & 3, (code >> 4) & 3};
+                const float f[3] = {q0.x, q0.y, q0.z};
+                float w[3][3];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) bspline_w(f[a], w[a]);
+#pragma unroll 1
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            const float wt = w[0][i] * w[1][jj] * w[2][k];
+                            const float d[3] = {(float)i - f[0], (float)jj - f[1], (float)k - f[2]};
+                            const int node = gidx(b[0] + i, b[1] + jj, b[2] + k);
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                atomicAdd(&S.t[r * GT3P + node],
+                                          __float2int_rn(wt * (vt[r] + Cs[3 * r] * d[0] + Cs[3 * r + 1] * d[1] + Cs[3 * r + 2] * d[2])));
+                        }
+            }
+        }
+        __syncthreads();
+        const float isc = 1.f / sc;
+        for (int t = tid; t < GT3; t += ADJ_THREADS) {
+            const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+            const int q = gidx(i, j, k);
+            const int a0 = S.t[q], a1 = S.t[GT3P + q], a2 = S.t[2 * GT3P + q];
+            if (a0 | a1 | a2) {
+                const int sl = S.slot[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+                if (sl >= 0)
+                    red_add_v4(gbar + (size_t)sl * BLK_NODES + node_loc(i, j, k), (float)a0 * isc, (float)a1 * isc,
+                               (float)a2 * isc, 0.f);
+                else
+                    set_err(D, ERRB_CAPACITY);
+            }
         }
         __syncthreads();
     }
@@ -451,7 +572,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
         for (int j = threadIdx.x; j < ch.z; j += blockDim.x) {
             const unsigned p = D.sorted[ch.y + j];
             ParticleIn P;
-            load_particle(D.rec + (size_t)p * REC_F4, P);
+            float4 rr[REC_F4];
+#pragma unroll
+            for (int w = 0; w < REC_F4; ++w) rr[w] = D.rec[(size_t)p * REC_F4 + w];
+            unpack_particle(rr, P);
             float f[3];
             int b[3];
             b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
@@ -639,7 +763,7 @@ static mpm_status dev_alloc(mpm_ctx *ctx, T **p, size_t count) {
 
 // consume any pending binning, then bin the current records
 static void rebin(mpm_ctx *ctx, cudaStream_t st) {
-    L_plan(ctx, 0, st);
+    if (ctx->bins_pending) L_plan(ctx, 0, st);
     L_bin(ctx, st);
 }
 
@@ -738,12 +862,10 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         if (cudaMemcpyAsync(D.rec, A.ckpt[(size_t)c], n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
         rebin(ctx, st);
-        for (int j = 0; j < len; ++j) {
-            if (cudaMemcpyAsync(A.tape + (size_t)j * ctx->cap * REC_F4, D.rec, n * REC_F4 * sizeof(float4),
-                                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
-            if (j < len - 1 && (s = run_substeps(ctx, 1, st))) return s;
-        }
+        if (cudaMemcpyAsync(A.tape, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
+        // one pipelined forward over the segment, copying each substep's result to the tape
+        if (len > 1 && (s = run_substeps(ctx, len - 1, st, A.tape, (size_t)ctx->cap * REC_F4))) return s;
         // reverse through the segment
         for (int j = len - 1; j >= 0; --j) {
             inject(s0 + j + 1);

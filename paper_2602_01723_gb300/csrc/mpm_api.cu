@@ -180,12 +180,20 @@ mpm_status mpm::ensure_chunks(mpm_ctx *ctx) {
 // ===========================================================================
 namespace mpm {
 
-void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st) { launch_plan(ctx->D, bump_mask, st); ++ctx->launches; }
+void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st) {
+    launch_plan(ctx->D, bump_mask, st);
+    ++ctx->launches;
+    ctx->bins_pending = false;
+}
 void L_prepare(mpm_ctx *ctx, int upd_par, int act_par, int do_sort, cudaStream_t st, int keep_momentum) {
     launch_prepare(ctx->D, upd_par, act_par, do_sort, keep_momentum, ctx->grid_small, st);
     ++ctx->launches;
 }
-void L_bin(mpm_ctx *ctx, cudaStream_t st) { launch_bin(ctx->D, st); ++ctx->launches; }
+void L_bin(mpm_ctx *ctx, cudaStream_t st) {
+    launch_bin(ctx->D, st);
+    ++ctx->launches;
+    ctx->bins_pending = true;
+}
 void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
     cudaEvent_t *ev = nullptr;
     if (ctx->trace_on) {
@@ -251,15 +259,21 @@ static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st) {
 }
 
 // forward of n substeps from the current state (bins must be valid);
-// leaves the state advanced and binned
-mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
+// leaves the state advanced and binned.  With tape != NULL the records after
+// substep s (s = 0 .. n_sub-1) are also copied to tape + (s+1) * tape_stride.
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, size_t tape_stride) {
     if (n_sub <= 0) return MPM_OK;
+    const size_t rec_bytes = (size_t)ctx->D.n * REC_F4 * sizeof(float4);
+    auto tape_copy = [&](int s) -> bool {
+        return !tape || cudaMemcpyAsync(tape + (size_t)(s + 1) * tape_stride, ctx->D.rec, rec_bytes,
+                                        cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    };
     L_plan(ctx, 3, st);               // epochs for buffer 0 (P2G below) and 1 (first fused substep)
     L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
     int s = 0;
     const int middle = n_sub - 1;
-    if (ctx->use_graph && !ctx->trace_on && middle >= 4) {
+    if (ctx->use_graph && !ctx->trace_on && !tape && middle >= 4) {
         cudaGraphExec_t ex = graph_pair(ctx, st);
         if (ex) {
             for (; s + 1 < middle; s += 2) {
@@ -279,7 +293,9 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
             L_prepare(ctx, par, -1, s > 0, st);           // sort for the latest plan
             L_substep(ctx, 2, par, 0, st);
         }
+        if (!tape_copy(s)) return fail(ctx, MPM_ERR_CUDA, "tape copy failed");
     }
+    ctx->bins_pending = true;     // the last substep binned the new positions
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return MPM_OK;

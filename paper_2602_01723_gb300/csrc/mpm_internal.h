@@ -97,6 +97,7 @@ struct mpm_ctx {
     cudaGraphExec_t graph2 = nullptr;
     long long graph_key = -1;     // (n, buffer generation) the graph was captured for
     long long generation = 0;     // bumped whenever a device buffer the kernels use is reallocated
+    bool bins_pending = false;    // a binning (counts / occupied list) awaits its plan
 };
 
 namespace mpm {
@@ -110,7 +111,7 @@ void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
 void L_bin(mpm_ctx *ctx, cudaStream_t st);
 void launch_reduce_by_material(const Dev &D, int n_mat, const float *per_particle, float *out, cudaStream_t st);
 mpm_status ensure_chunks(mpm_ctx *ctx);
-mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape = nullptr, size_t tape_stride = 0);
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);
 mpm_status ctx_check(mpm_ctx *ctx, cudaStream_t st);
