@@ -116,6 +116,24 @@ def dist_setup(n_gpus):
     return None, 0, 1, 0
 
 
+def max_over_ranks(local_ms, dist, device=None):
+    """The slowest rank's time: whole-job throughput divides by it."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_units(n_units, rank, world):
+    """Contiguous, near-equal shard [lo, hi) of n_units independent problems
+    (instances of a batch) for one rank; no data moves between shards."""
+    base, extra = divmod(n_units, world)
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
 def oracle_rate(sc, n_sub):
     """Timed FP64 oracle on the first n_sub substeps of the workload."""
     import oracle as orc
@@ -223,11 +241,7 @@ def run_ours(args):
     sim.sync()
     tr = sim.trace(False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = max_over_ranks(sum(step_ms), dist, dev)
     value = world * n * S * args.steps / (tot_ms * 1e-3)
 
     # roofline of the dominant kernel: the fused G2P + update + P2G kernel
@@ -369,11 +383,7 @@ def fwd_bwd(args, dev, flush, world, dist):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     launches = sim.stats()["launches"] - l0
-    tot = sum(ms)
-    if dist is not None:
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot = float(t.item())
+    tot = max_over_ranks(sum(ms), dist, dev)
     value = world * n * S * args.steps / (tot * 1e-3)
     peak, _ = load_peaks()
     sim.close()

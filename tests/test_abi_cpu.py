@@ -1,0 +1,84 @@
+"""CPU checks of the C ABI: libmpm.so builds, loads without a GPU, exports
+every entry point include/mpm.h declares, and rejects bad arguments before
+touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2602_01723_gb300.build import build
+    build()
+    from paper_2602_01723_gb300 import _lib
+    _lib.lib()
+    return _lib
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "mpm.h")).read()
+    return sorted(set(re.findall(r"MPM_API\s+[\w\s\*]+?\b(mpm_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for required in ("mpm_create", "mpm_load_particles", "mpm_step", "mpm_backward", "mpm_destroy"):
+        assert required in names
+    assert len(names) >= 16
+
+
+def test_library_exports_every_declared_symbol(L):
+    so = ctypes.CDLL(L.SO)
+    for name in declared_symbols():
+        assert hasattr(so, name), name
+        assert name in L.SIGNATURES, name     # the binding knows its signature
+
+
+def test_default_options(L):
+    o = L.mpm_default_options()
+    assert o.n_instances == 1 and o.bound == 3 and o.ckpt_every == 20 and o.scatter == 1
+    assert list(o.walls) == [1, 1, 2, 1, 1, 1]
+
+
+def test_create_rejects_bad_arguments_without_a_device(L):
+    lib = L.lib()
+    out = ctypes.c_void_p()
+    mats = (L.mpm_material * 1)(L.mpm_material(0, 0, 1e4, 0.3, 1.0, 0.0, 30.0))
+    g = (ctypes.c_float * 3)(0, -9.8, 0)
+    bad_res = [(30, 32, 32), (32, 32, 4), (0, 32, 32)]
+    for r in bad_res:
+        st = lib.mpm_create((ctypes.c_int32 * 3)(*r), 1 / 32, 1e-4, g, mats, 1, None, ctypes.byref(out))
+        assert st == 1 and not out.value          # MPM_ERR_INVALID_ARG, nothing created
+    st = lib.mpm_create((ctypes.c_int32 * 3)(32, 32, 32), -1.0, 1e-4, g, mats, 1, None, ctypes.byref(out))
+    assert st == 1
+    bad = (L.mpm_material * 1)(L.mpm_material(0, 5, 1e4, 0.3, 1.0, 0.0, 30.0))     # unknown plasticity
+    st = lib.mpm_create((ctypes.c_int32 * 3)(32, 32, 32), 1 / 32, 1e-4, g, bad, 1, None, ctypes.byref(out))
+    assert st == 1
+    assert b"material" in lib.mpm_last_error(None)
+    assert lib.mpm_destroy(None) == 0            # NULL-safe
+
+
+def test_entry_points_reject_a_null_context(L):
+    lib = L.lib()
+    assert lib.mpm_step(None, 1, 0, None) == 1
+    assert lib.mpm_sync(None, None) == 1
+    assert lib.mpm_backward(None, 0, None, None, None, None, None) == 1
+    assert lib.mpm_set_tuning(None, 1, 128, 1) == 1
+
+
+def test_noalloc_rejects_oversize_grids_before_any_device_work(L):
+    lib = L.lib()
+    h = np.zeros(64, dtype=np.float32)
+    p = ctypes.c_void_p(h.ctypes.data)
+    mats = (L.mpm_material * 1)(L.mpm_material(0, 0, 1e4, 0.3, 1.0, 0.0, 30.0))
+    st = lib.mpm_substep_noalloc((ctypes.c_int32 * 3)(128, 128, 32), 1 / 128, 1e-4, (ctypes.c_float * 3)(0, -9.8, 0),
+                                 mats, 1, None, 1, p, p, p, p, p, p, p, p, p, p, None)
+    assert st == 8                                # MPM_ERR_CAPACITY
+    st = lib.mpm_substep_noalloc((ctypes.c_int32 * 3)(32, 32, 32), 1 / 32, 1e-4, (ctypes.c_float * 3)(0, -9.8, 0),
+                                 mats, 17, None, 1, p, p, p, p, p, p, p, p, p, p, None)
+    assert st == 1                                # more than 16 materials
