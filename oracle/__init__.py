@@ -57,6 +57,11 @@ class _Mat(ctypes.Structure):
                 ("elastic", _PI), ("plastic", _PI)]
 
 
+class _BgdoOpt(ctypes.Structure):
+    _fields_ = [("delta_target", ctypes.c_double), ("w", ctypes.c_double), ("per_material", ctypes.c_int),
+                ("delta_pre_step", ctypes.c_int)]
+
+
 def lib():
     global _lib
     with _lock:
@@ -79,6 +84,8 @@ def lib():
             L.orc_run.argtypes = [cp, ctypes.c_long, _P, _P, _P, _P, mp, ctypes.c_int, _P]
             L.orc_substep_adjoint.argtypes = [cp, ctypes.c_long, _P, mp, _P, _P, _P]
             L.orc_backward.argtypes = [cp, ctypes.c_long, mp, ctypes.c_int, _P, ctypes.c_int, _PI, _P, _P, _P]
+            L.orc_bgdo.argtypes = [cp, ctypes.c_long, ctypes.c_int, _P, mp, _PI, ctypes.c_int,
+                                   ctypes.POINTER(_BgdoOpt), _P, _P, _P]
             _lib = L
     return _lib
 
@@ -340,3 +347,24 @@ def trajectory_loss(frames_x, target_x):
     nf, n = fx.shape[0], fx.shape[1]
     d = fx - tx
     return float(np.sum(d * d) / (nf * n)), 2.0 * d / (nf * n)
+
+
+def bgdo(cfg: Cfg, keys, mat: Material, label=None, delta_target=0.1, w=None, per_material=False,
+         delta_pre_step=False):
+    """BGDO stage 2 (§4.3, Algorithm 2, App. F) from key-frame states.
+
+    keys: list of states (dicts).  w=None takes eta = min(1, 0.1 log(1+E)).
+    Returns dict(G (n,), log_E (n,) = logE - G, g_tau (K,n), delta (K,n))."""
+    K = len(keys)
+    n = len(keys[0]["x"])
+    kp = _f64(np.stack([pack(k) for k in keys]))
+    lab = np.ascontiguousarray(np.zeros(n, np.int32) if label is None else np.asarray(label, dtype=np.int32))
+    n_lab = int(lab.max()) + 1 if n else 0
+    opt = _BgdoOpt(float(delta_target), -1.0 if w is None else float(w), int(bool(per_material)),
+                   int(bool(delta_pre_step)))
+    G = np.zeros(n)
+    gt = np.zeros((K, n))
+    dl = np.zeros((K, n))
+    _check(lib().orc_bgdo(cfg.ptr, n, K, _d(kp), mat.ptr, lab.ctypes.data_as(_PI), n_lab, ctypes.byref(opt),
+                          _d(G), _d(gt), _d(dl)))
+    return {"G": G, "log_E": mat.logE - G, "g_tau": gt, "delta": dl}

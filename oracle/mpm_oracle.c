@@ -19,7 +19,10 @@
  *     Neo-Hookean (App. A, eq. neo_hookean, times F^T);
  *   - Lame parameters from (E, nu) (App. B.1);
  *   - von Mises and Drucker-Prager return maps on log singular values
- *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2).
+ *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2);
+ *   - BGDO stage 2: key-frame pseudo step, stress-norm gradient in log E,
+ *     log compression and Frobenius deformation guidance (§4.3, Algorithm 2,
+ *     App. F).
  * Readings where the paper is silent are listed in the design doc (interpolation
  * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
  * delta-gamma of Klar et al. 2016, the 1e-4 floor before log).
@@ -872,5 +875,99 @@ int orc_backward(const orc_cfg *cfg, long n, const orc_material *mat, int n_sub,
     }
     memcpy(adj0, a, 24 * n * sizeof(double));
     free(a); free(b);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BGDO stage 2: the gradient-based backward optimisation of log E from      */
+/* stored key frames (§4.3 "Optimization Algorithm", Algorithm 2, App. F).   */
+/*                                                                          */
+/* For every key frame k with state (x, v, C, F)_k and every particle p:     */
+/*   s_p      = |tau_p(F_p, log E_p)|_F, tau the Kirchhoff stress of the     */
+/*              particle's elastic model;                                    */
+/*   g_tau,p  = d s_p / d log E_p (the derivative is taken through the Lame   */
+/*              parameters, d mu / d log E = mu, d lambda / d log E = lambda  */
+/*              at fixed nu, App. B.1);                                      */
+/*   gt_p     = log(1 + |g_tau,p|)                       (App. F.3);         */
+/*   F'_p     = the F of one pseudo substep from the key frame, after the     */
+/*              return map (Algorithm 2, stage 2);                           */
+/*   delta_p  = |F'_p - I|_F                             (App. F.2);         */
+/*   eta_p    = min(1, 0.1 log(1 + E_p)) (§4.3 eq. eq_target), or the fixed   */
+/*              weight w of Algorithm 2 when w >= 0;                          */
+/*   G_p     += (eta_p gt_p - (1 - eta_p)(delta_p - delta_target)) / K.      */
+/* Then log E_p <- log E_p - G_p (done by the caller).  Readings: the norms   */
+/* are per particle (App. F.2 defines delta on one 3x3 F'); compression      */
+/* is applied per key frame before the average (Algorithm 2); with           */
+/* per_material the G of all particles carrying the same label is replaced   */
+/* by its mean (the spatial average App. F.3 mentions).  delta_pre_step      */
+/* takes delta from the key frame's own F, the d_F of the §4.3 equation.     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double delta_target;
+    double w;
+    int per_material;
+    int delta_pre_step;
+} orc_bgdo_opt;
+
+/* d tau / d log E at fixed nu: tau is linear in (mu, lambda) for every model
+ * here, so it is mu tau(F; 1, 0) + lambda tau(F; 0, 1). */
+static int kirchhoff_dlogE(int model, const double F[9], double mu, double lam, double dtau[9]) {
+    double a[9], b[9];
+    int st = orc_kirchhoff(model, F, 1.0, 0.0, a);
+    if (st) return st;
+    st = orc_kirchhoff(model, F, 0.0, 1.0, b);
+    if (st) return st;
+    for (int i = 0; i < 9; ++i) dtau[i] = mu * a[i] + lam * b[i];
+    return ORC_OK;
+}
+
+/* keys: n_keys packed states (n x 24 each).  label/n_labels are used only with
+ * per_material.  g_tau and delta (n_keys x n, nullable) receive the per-key
+ * signals.  G (n) receives the update. */
+int orc_bgdo(const orc_cfg *cfg, long n, int n_keys, const double *keys, const orc_material *mat,
+             const int *label, int n_labels, const orc_bgdo_opt *opt, double *G, double *g_tau,
+             double *delta) {
+    double *x = (double *)malloc(3 * n * sizeof(double)), *v = (double *)malloc(3 * n * sizeof(double));
+    double *C = (double *)malloc(9 * n * sizeof(double)), *F = (double *)malloc(9 * n * sizeof(double));
+    double *F0 = (double *)malloc(9 * n * sizeof(double));
+    int st = ORC_OK;
+    for (long p = 0; p < n; ++p) G[p] = 0.0;
+    for (int k = 0; k < n_keys && !st; ++k) {
+        unpack_state(keys + (size_t)k * n * 24, n, x, v, C, F);
+        memcpy(F0, F, 9 * n * sizeof(double));
+        if (!opt->delta_pre_step) st = orc_substep(cfg, n, x, v, C, F, mat);   /* pseudo step */
+        for (long p = 0; p < n && !st; ++p) {
+            double mu, lam, tau[9], dtau[9];
+            particle_lame(mat, p, &mu, &lam);
+            st = orc_kirchhoff(mat->elastic[p], F0 + 9 * p, mu, lam, tau);
+            if (!st) st = kirchhoff_dlogE(mat->elastic[p], F0 + 9 * p, mu, lam, dtau);
+            if (st) break;
+            double s = sqrt(m_dot(tau, tau));
+            double g = s > 0.0 ? m_dot(tau, dtau) / s : 0.0;
+            double gt = log(1.0 + fabs(g));
+            const double *Fn = opt->delta_pre_step ? F0 + 9 * p : F + 9 * p;
+            double d2 = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    double t = Fn[3 * i + j] - (i == j ? 1.0 : 0.0);
+                    d2 += t * t;
+                }
+            double dl = sqrt(d2);
+            double E = exp(mat->logE[p]);
+            double eta = opt->w >= 0.0 ? opt->w : fmin(1.0, 0.1 * log(1.0 + E));
+            G[p] += (eta * gt - (1.0 - eta) * (dl - opt->delta_target)) / n_keys;
+            if (g_tau) g_tau[(size_t)k * n + p] = g;
+            if (delta) delta[(size_t)k * n + p] = dl;
+        }
+    }
+    if (!st && opt->per_material) {
+        double *sum = (double *)calloc(n_labels, sizeof(double));
+        long *cnt = (long *)calloc(n_labels, sizeof(long));
+        for (long p = 0; p < n; ++p) { sum[label[p]] += G[p]; cnt[label[p]] += 1; }
+        for (long p = 0; p < n; ++p) G[p] = sum[label[p]] / cnt[label[p]];
+        free(sum); free(cnt);
+    }
+    free(x); free(v); free(C); free(F); free(F0);
     return st;
 }
