@@ -351,7 +351,7 @@ def trajectory_loss(frames_x, target_x):
 
 def bgdo(cfg: Cfg, keys, mat: Material, label=None, delta_target=0.1, w=None, per_material=False,
          delta_pre_step=False):
-    """BGDO stage 2 (§4.3, Algorithm 2, App. F) from key-frame states.
+    """BGDO stage 2 (§4.3, Algorithm 1, App. F) from key-frame states.
 
     keys: list of states (dicts).  w=None takes eta = min(1, 0.1 log(1+E)).
     Returns dict(G (n,), log_E (n,) = logE - G, g_tau (K,n), delta (K,n))."""

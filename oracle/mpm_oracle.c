@@ -21,7 +21,7 @@
  *   - von Mises and Drucker-Prager return maps on log singular values
  *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2);
  *   - BGDO stage 2: key-frame pseudo step, stress-norm gradient in log E,
- *     log compression and Frobenius deformation guidance (§4.3, Algorithm 2,
+ *     log compression and Frobenius deformation guidance (§4.3, Algorithm 1,
  *     App. F).
  * Readings where the paper is silent are listed in the design doc (interpolation
  * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
@@ -880,7 +880,7 @@ int orc_backward(const orc_cfg *cfg, long n, const orc_material *mat, int n_sub,
 
 /* ------------------------------------------------------------------------ */
 /* BGDO stage 2: the gradient-based backward optimisation of log E from      */
-/* stored key frames (§4.3 "Optimization Algorithm", Algorithm 2, App. F).   */
+/* stored key frames (§4.3 "Optimization Algorithm", Algorithm 1, App. F).   */
 /*                                                                          */
 /* For every key frame k with state (x, v, C, F)_k and every particle p:     */
 /*   s_p      = |tau_p(F_p, log E_p)|_F, tau the Kirchhoff stress of the     */
@@ -890,14 +890,14 @@ int orc_backward(const orc_cfg *cfg, long n, const orc_material *mat, int n_sub,
 /*              at fixed nu, App. B.1);                                      */
 /*   gt_p     = log(1 + |g_tau,p|)                       (App. F.3);         */
 /*   F'_p     = the F of one pseudo substep from the key frame, after the     */
-/*              return map (Algorithm 2, stage 2);                           */
+/*              return map (Algorithm 1, Stage 2);                           */
 /*   delta_p  = |F'_p - I|_F                             (App. F.2);         */
 /*   eta_p    = min(1, 0.1 log(1 + E_p)) (§4.3 eq. eq_target), or the fixed   */
-/*              weight w of Algorithm 2 when w >= 0;                          */
+/*              weight w of Algorithm 1 when w >= 0;                          */
 /*   G_p     += (eta_p gt_p - (1 - eta_p)(delta_p - delta_target)) / K.      */
 /* Then log E_p <- log E_p - G_p (done by the caller).  Readings: the norms   */
 /* are per particle (App. F.2 defines delta on one 3x3 F'); compression      */
-/* is applied per key frame before the average (Algorithm 2); with           */
+/* is applied per key frame before the average (Algorithm 1); with           */
 /* per_material the G of all particles carrying the same label is replaced   */
 /* by its mean (the spatial average App. F.3 mentions).  delta_pre_step      */
 /* takes delta from the key frame's own F, the d_F of the §4.3 equation.     */

@@ -1,4 +1,4 @@
-"""Pins of the oracle's BGDO stage 2 (§4.3, Algorithm 2, App. F) against
+"""Pins of the oracle's BGDO stage 2 (§4.3, Algorithm 1, App. F) against
 closed forms: the stress-gradient of a model linear in E, central differences
 through the Lame map, rest and rigid-rotation key frames, the fixed-weight
 limits and the per-material average."""
