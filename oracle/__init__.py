@@ -84,6 +84,7 @@ def lib():
             L.orc_run.argtypes = [cp, ctypes.c_long, _P, _P, _P, _P, mp, ctypes.c_int, _P]
             L.orc_substep_adjoint.argtypes = [cp, ctypes.c_long, _P, mp, _P, _P, _P]
             L.orc_backward.argtypes = [cp, ctypes.c_long, mp, ctypes.c_int, _P, ctypes.c_int, _PI, _P, _P, _P]
+            L.orc_covariance.argtypes = [ctypes.c_long, _P, _P, _P]
             L.orc_bgdo.argtypes = [cp, ctypes.c_long, ctypes.c_int, _P, mp, _PI, ctypes.c_int,
                                    ctypes.POINTER(_BgdoOpt), _P, _P, _P]
             _lib = L
@@ -368,3 +369,19 @@ def bgdo(cfg: Cfg, keys, mat: Material, label=None, delta_target=0.1, w=None, pe
     _check(lib().orc_bgdo(cfg.ptr, n, K, _d(kp), mat.ptr, lab.ctypes.data_as(_PI), n_lab, ctypes.byref(opt),
                           _d(G), _d(gt), _d(dl)))
     return {"G": G, "log_E": mat.logE - G, "g_tau": gt, "delta": dl}
+
+
+def covariance(F, cov0):
+    """Sigma(t) = F Sigma F^T per particle (§3.2); cov as (n,6) xx xy xz yy yz zz."""
+    F = _f64(F, (-1, 3, 3))
+    n = len(F)
+    c0 = _f64(cov0, (n, 6))
+    out = np.zeros((n, 6))
+    lib().orc_covariance(n, _d(F), _d(c0), _d(out))
+    return out
+
+
+def sym33(c):
+    """(n,6) xx xy xz yy yz zz -> (n,3,3)."""
+    c = np.asarray(c, dtype=np.float64).reshape(-1, 6)
+    return np.stack([c[:, [0, 1, 2]], c[:, [1, 3, 4]], c[:, [2, 4, 5]]], axis=1)

@@ -22,7 +22,9 @@
  *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2);
  *   - BGDO stage 2: key-frame pseudo step, stress-norm gradient in log E,
  *     log compression and Frobenius deformation guidance (§4.3, Algorithm 1,
- *     App. F).
+ *     App. F);
+ *   - the Gaussian kernel's covariance after deformation, F Sigma F^T
+ *     (§3.2, with Sigma = R S S^T R^T of §3.1).
  * Readings where the paper is silent are listed in the design doc (interpolation
  * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
  * delta-gamma of Klar et al. 2016, the 1e-4 floor before log).
@@ -970,4 +972,27 @@ int orc_bgdo(const orc_cfg *cfg, long n, int n_keys, const double *keys, const o
     }
     free(x); free(v); free(C); free(F); free(F0);
     return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian-kernel covariance carried by a particle (§3.1, §3.2): the        */
+/* kernel deforms with the particle, Sigma(t) = F(t) Sigma F(t)^T.           */
+/* cov0 and out hold the symmetric 3x3 as xx xy xz yy yz zz per particle.    */
+/* ------------------------------------------------------------------------ */
+
+static void sym_unpack(const double *c, double S[9]) {
+    S[0] = c[0]; S[1] = c[1]; S[2] = c[2];
+    S[3] = c[1]; S[4] = c[3]; S[5] = c[4];
+    S[6] = c[2]; S[7] = c[4]; S[8] = c[5];
+}
+
+void orc_covariance(long n, const double *F, const double *cov0, double *out) {
+    for (long p = 0; p < n; ++p) {
+        double S[9], FS[9], T[9];
+        sym_unpack(cov0 + 6 * p, S);
+        m_mul(FS, F + 9 * p, S);
+        m_mul_nt(T, FS, F + 9 * p);
+        double *o = out + 6 * p;
+        o[0] = T[0]; o[1] = T[1]; o[2] = T[2]; o[3] = T[4]; o[4] = T[5]; o[5] = T[8];
+    }
 }

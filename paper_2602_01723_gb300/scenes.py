@@ -382,3 +382,42 @@ WORKLOADS = {
     "batch_64": batch_64,
     "large_2m": large_2m,
 }
+
+
+def key_frames(sc: Scene, n_keys=3, k_seed=40, vs=0.5, cs=5.0, fs=0.05):
+    """n_keys synthetic key-frame states (v, C, F) at the scene's positions:
+    the scene velocity plus N(0, vs^2) noise, an affine field N(0, cs^2) and a
+    deformation gradient R_z(0.3 k) (I + N(0, fs^2)).  They stand in for the
+    snapshots a forward run would store (Algorithm 1, Stage 1)."""
+    rng = _rng(k_seed)
+    n = sc.n
+    out = []
+    for k in range(n_keys):
+        th = 0.3 * k
+        Rz = np.array([[math.cos(th), -math.sin(th), 0.0], [math.sin(th), math.cos(th), 0.0], [0.0, 0.0, 1.0]])
+        v = sc.v + vs * rng.standard_normal((n, 3))
+        C = cs * rng.standard_normal((n, 3, 3))
+        F = np.einsum("ij,njk->nik", Rz, np.eye(3) + fs * rng.standard_normal((n, 3, 3)))
+        out.append((_f32(v), _f32(C), _f32(F)))
+    return out
+
+
+def gaussian_covariances(sc: Scene, k_seed=50):
+    """A Gaussian kernel per particle, Sigma = R S S^T R^T (§3.1) with a
+    uniformly random rotation R and flat splat scales S = diag(a, b, 0.1 a')
+    where a, b ~ U(0.3, 1) dx/2 (surface-like 3DGS kernels).  Returned as
+    (n, 6) float32 xx xy xz yy yz zz."""
+    rng = _rng(k_seed)
+    n = sc.n
+    half = 0.5 * sc.dx
+    q = rng.standard_normal((n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    a, b, c, d = q.T
+    R = np.stack([np.stack([a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)], -1),
+                  np.stack([2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)], -1),
+                  np.stack([2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d], -1)], 1)
+    s = np.stack([rng.uniform(0.3, 1.0, n) * half, rng.uniform(0.3, 1.0, n) * half,
+                  0.1 * rng.uniform(0.3, 1.0, n) * half], 1)
+    M = R * s[:, None, :]
+    S = M @ M.transpose(0, 2, 1)
+    return _f32(np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1))
