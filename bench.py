@@ -45,6 +45,13 @@ FB_WORKLOAD = "ball_50k"
 # reverse substep (tape state read by the recomputed P2G, the G2P adjoint and
 # the P2G adjoint, adjoint state in and out, parameter gradients: ~480 B)
 FB_BYTES_PER_PS = 880.0
+# BGDO stage 2 per particle and key frame: one pseudo substep (200 B) and the
+# signal pass (key-frame F and Lame pair 44 B, post-step F 36 B, G read and
+# written 8 B); the copy of the key frame is not counted
+BGDO_BYTES_PER_PK = 288.0
+# deformed covariance per particle: F (36 B) and rest covariance (24 B) read,
+# covariance (24 B) written
+COV_BYTES_PER_P = 84.0
 
 
 def load_peaks():
@@ -305,6 +312,7 @@ def run_ours(args):
         err["note"] = "teacher-forced: FP32 GPU vs FP64 oracle from the same state after %d substeps" % S
 
     fb = fwd_bwd(args, dev, flush, world, dist)
+    bg = bgdo_leg(args, sim, sc, (x0, v0, vol, mid), flush)
 
     if rank == 0:
         cpu_v, cpu_t = oracle_rate(sc, ORACLE_SAMPLE_SUBSTEPS)
@@ -331,12 +339,72 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "err_vs_fp64": err,
             "fwd_bwd": fb,
+            "bgdo": bg,
         }
         print(json.dumps(line), flush=True)
     sim.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def bgdo_leg(args, sim, sc, init, flush):
+    """One BGDO iteration on the same scene (§4.3, Algorithm 1): stage 1 is
+    the full forward with key frames at substeps 0, S/2 and S; stage 2 the
+    three pseudo substeps and the log-E update.  Also times the export of the
+    deformed Gaussian covariances F Sigma F^T (§3.2)."""
+    import torch
+    from paper_2602_01723_gb300 import _lib as L
+    from paper_2602_01723_gb300.sim import _p, _stream
+    x0, v0, vol, mid = init
+    n, S = sc.n, sc.n_substeps
+
+    def stage1():
+        L.mpm_load_particles(sim.ctx, n, _p(x0), _p(v0), None, None, _p(vol), _p(mid), None, None, _stream())
+        sim.snapshot(0)
+        sim.step(S // 2)
+        sim.snapshot(1)
+        sim.step(S - S // 2)
+        sim.snapshot(2)
+
+    def timed(fn, reps):
+        ms = []
+        for k in range(reps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    stage1()
+    sim.bgdo([0, 1, 2])
+    sim.sync()
+    s1 = timed(stage1, max(1, min(args.steps, 2)))
+    out = {}
+
+    def stage2():
+        out.update(sim.bgdo([0, 1, 2]))
+    s2 = timed(stage2, max(3, args.steps))
+    sim.sync()
+    peak, _ = load_peaks()
+    pk = n * 3 / (s2 * 1e-3)
+    cov0 = torch.zeros((n, 6), device=x0.device)
+    cov0[:, 0] = cov0[:, 3] = cov0[:, 5] = 1e-6
+    sim.load_covariance(cov0)
+    cov = torch.empty((n, 6), device=x0.device)
+    cms = timed(lambda: sim.covariance(out=cov), max(3, args.steps))
+    return {"workload": sc.name, "particles": n, "keys": 3, "stage1_ms": s1, "stage2_ms": s2,
+            "iteration_ms": s1 + s2, "particle_keys_per_s": pk,
+            "stage2_bytes_per_particle_key": BGDO_BYTES_PER_PK,
+            "stage2_hbm_frac": pk * BGDO_BYTES_PER_PK / 1e9 / peak,
+            "G_finite": bool(torch.isfinite(out["G"]).all().item()),
+            "covariance": {"us": cms * 1e3, "bytes_per_particle": COV_BYTES_PER_P,
+                           "hbm_frac": n * COV_BYTES_PER_P / (cms * 1e-3) / 1e9 / peak},
+            "note": "CUDA events, medians; stage 1 includes the three snapshot copies"}
 
 
 def fwd_bwd(args, dev, flush, world, dist):

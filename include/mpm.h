@@ -183,6 +183,70 @@ MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, 
  * Synchronises the stream. */
 MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3], void *stream);
 
+/* ---------------------------------------------------------------------------
+ * BGDO (§4.3 "Optimization Algorithm"; Algorithm 1, Stage 2; App. F)
+ *
+ * Stage 1 is the ordinary forward (mpm_step) with key-frame snapshots taken
+ * by mpm_snapshot.  Stage 2 (mpm_bgdo) runs, from every key frame k, one
+ * pseudo substep with the current parameters and accumulates per particle p
+ *     g_tau = d |tau_p|_F / d log E_p   (= |tau_p|_F: tau is linear in the
+ *                                         Lame parameters, App. B.1)
+ *     delta = |F'_p - I|_F              (F' after the pseudo substep and the
+ *                                         return map, App. F.2)
+ *     eta   = min(1, 0.1 log(1 + E_p))  (§4.3, eq. eq_target) or a fixed w
+ *     G_p  += (eta log(1 + |g_tau|) - (1 - eta)(delta - delta_target)) / K
+ * and the update log E_p <- log E_p - G_p (App. F.3).
+ * ------------------------------------------------------------------------ */
+#define MPM_MAX_SNAPSHOTS 8
+
+/* Copies the current state of every particle, with its mass, volume and
+ * material parameters, into key-frame slot 0 <= slot < MPM_MAX_SNAPSHOTS
+ * (library-owned device memory, 128 bytes per particle, allocated on first
+ * use of the slot).  A slot can be used by mpm_bgdo while the particle count
+ * equals the count at the snapshot; the pseudo substep then uses the
+ * parameters stored with the snapshot.  Enqueued on the stream. */
+MPM_API mpm_status mpm_snapshot(mpm_ctx *ctx, int32_t slot, void *stream);
+
+typedef struct {
+    float delta_target;      /* deformation target (App. F.2); default 0.1 */
+    float w;                 /* < 0: eta = min(1, 0.1 log(1 + E)) per particle (default -1);
+                                in [0, 1]: the fixed balancing weight w of Algorithm 1 */
+    int32_t per_material;    /* 1: G averaged over the particles of each material id */
+    int32_t delta_pre_step;  /* 1: delta from the key frame's own F (the d_F of §4.3)
+                                instead of the post-step F' (no pseudo substep runs) */
+    int32_t reserved[4];     /* zero */
+} mpm_bgdo_options;
+
+MPM_API mpm_status mpm_bgdo_default_options(mpm_bgdo_options *opt);
+
+/* BGDO stage 2 over n_keys (1..MPM_MAX_SNAPSHOTS) key-frame slots (host
+ * array).  opt may be NULL (defaults).  Outputs, each nullable, in the
+ * caller's particle order, host or device: G (n), log_E (n: log E_p - G_p
+ * with E_p the current particle's modulus, the updated parameter to load for
+ * the next iteration), g_tau and delta (n_keys x n, the per-key signals).
+ * The current state and the recorded trajectory are left unchanged.
+ * Synchronises the stream when an output is a host pointer.  MPM_ERR_STATE
+ * when a slot is empty or was taken with another particle count. */
+MPM_API mpm_status mpm_bgdo(mpm_ctx *ctx, int32_t n_keys, const int32_t *slots, const mpm_bgdo_options *opt,
+                            float *G, float *log_E, float *g_tau, float *delta, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Gaussian kernels (§3.1: each splat is a Gaussian with covariance
+ * Sigma = R S S^T R^T; §3.2: it deforms with its particle,
+ * Sigma(t) = F(t) Sigma F(t)^T).  Covariances are symmetric 3x3 stored as
+ * n x 6 floats: xx xy xz yy yz zz, in the caller's particle order.
+ * ------------------------------------------------------------------------ */
+
+/* Sets the rest covariance Sigma of every currently loaded particle (n x 6,
+ * host or device; copied).  Valid while the particle count is unchanged.
+ * Enqueued on the stream. */
+MPM_API mpm_status mpm_load_covariance(mpm_ctx *ctx, const float *cov0, void *stream);
+
+/* Writes F Sigma F^T of every particle's current F into cov (n x 6, host or
+ * device).  MPM_ERR_STATE when no rest covariances match the particle count.
+ * Enqueued on the stream; does not synchronise. */
+MPM_API mpm_status mpm_get_covariance(mpm_ctx *ctx, float *cov, void *stream);
+
 /* Diagnostic: P2G of the current state into dense device arrays m
  * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at
  * ((b * R0 + I) * R1 + J) * R2 + K) and mv (3 floats per node); the particle

@@ -34,6 +34,13 @@ class mpm_options(ctypes.Structure):
                 ("scatter", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
 
 
+class mpm_bgdo_options(ctypes.Structure):
+    _fields_ = [("delta_target", ctypes.c_float), ("w", ctypes.c_float), ("per_material", ctypes.c_int32),
+                ("delta_pre_step", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+MPM_MAX_SNAPSHOTS = 8
+
 _ctx_p = ctypes.c_void_p
 _vp = ctypes.c_void_p
 _i32p = ctypes.POINTER(ctypes.c_int32)
@@ -57,6 +64,12 @@ SIGNATURES = {
     "mpm_debug_p2g": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
     "mpm_trace": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _i64p]),
     "mpm_reduce_by_material": (ctypes.c_int, [_ctx_p, _vp, _vp, _vp]),
+    "mpm_snapshot": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _vp]),
+    "mpm_bgdo_default_options": (ctypes.c_int, [ctypes.POINTER(mpm_bgdo_options)]),
+    "mpm_bgdo": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, ctypes.POINTER(mpm_bgdo_options), _vp, _vp, _vp,
+                                _vp, _vp]),
+    "mpm_load_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
+    "mpm_get_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
     "mpm_set_tuning": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mpm_autotune": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, _vp]),
     "mpm_substep_noalloc": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
@@ -181,3 +194,26 @@ def mpm_autotune(ctx, n_substeps, stream):
 
 def mpm_debug_p2g(ctx, m, mv, stream):
     check(lib().mpm_debug_p2g(ctx, m, mv, stream), ctx)
+
+
+def mpm_snapshot(ctx, slot, stream):
+    check(lib().mpm_snapshot(ctx, int(slot), stream), ctx)
+
+
+def mpm_bgdo(ctx, slots, delta_target, w, per_material, delta_pre_step, G, log_E, g_tau, delta, stream):
+    o = mpm_bgdo_options()
+    check(lib().mpm_bgdo_default_options(ctypes.byref(o)))
+    o.delta_target = float(delta_target)
+    o.w = -1.0 if w is None else float(w)
+    o.per_material = int(bool(per_material))
+    o.delta_pre_step = int(bool(delta_pre_step))
+    sl = (ctypes.c_int32 * len(slots))(*[int(k) for k in slots])
+    check(lib().mpm_bgdo(ctx, len(slots), sl, ctypes.byref(o), G, log_E, g_tau, delta, stream), ctx)
+
+
+def mpm_load_covariance(ctx, cov0, stream):
+    check(lib().mpm_load_covariance(ctx, cov0, stream), ctx)
+
+
+def mpm_get_covariance(ctx, cov, stream):
+    check(lib().mpm_get_covariance(ctx, cov, stream), ctx)

@@ -762,10 +762,6 @@ static mpm_status dev_alloc(mpm_ctx *ctx, T **p, size_t count) {
 }
 
 // consume any pending binning, then bin the current records
-static void rebin(mpm_ctx *ctx, cudaStream_t st) {
-    if (ctx->bins_pending) L_plan(ctx, 0, st);
-    L_bin(ctx, st);
-}
 
 // reverse of one substep whose input state is `state`
 static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *aout, cudaStream_t st) {

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 #include <string>
@@ -299,6 +300,11 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
     return MPM_OK;
+}
+
+void rebin(mpm_ctx *ctx, cudaStream_t st) {
+    if (ctx->bins_pending) L_plan(ctx, 0, st);
+    L_bin(ctx, st);
 }
 
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m) { return fail(ctx, s, m); }
@@ -597,6 +603,8 @@ MPM_API mpm_status mpm_destroy(mpm_ctx *ctx) {
     dfree(ctx->mel); dfree(ctx->mpl);
     dfree(ctx->stage);
     free_adjoint(ctx->adj);
+    for (int k = 0; k < MPM_MAX_SNAPSHOTS; ++k) dfree(ctx->snap[k]);
+    dfree(ctx->bgdo_work); dfree(ctx->bgdo_G); dfree(ctx->bgdo_sum); dfree(ctx->cov0);
     for (int m = 0; m < 3; ++m)
         for (cudaEvent_t e : ctx->trace_ev[m]) cudaEventDestroy(e);
     if (ctx->graph2) cudaGraphExecDestroy(ctx->graph2);
@@ -696,6 +704,153 @@ MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3]
 // P2G of the current state into dense caller arrays m (n_inst*R0*R1*R2) and
 // mv (x3); the particle state is left unchanged.  Diagnostic entry point used
 // by the teacher-forced parity tests.
+MPM_API mpm_status mpm_snapshot(mpm_ctx *ctx, int32_t slot, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (slot < 0 || slot >= MPM_MAX_SNAPSHOTS) return fail(ctx, MPM_ERR_INVALID_ARG, "snapshot slot out of range");
+    if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state (load particles first)");
+    mpm_status s;
+    if (!ctx->snap[slot] || ctx->snap_cap[slot] < ctx->cap) {
+        if ((s = dalloc(ctx, &ctx->snap[slot], (size_t)ctx->cap * REC_F4, false))) return s;
+        ctx->snap_cap[slot] = ctx->cap;
+    }
+    CK(cudaMemcpyAsync(ctx->snap[slot], ctx->D.rec, (size_t)ctx->D.n * REC_F4 * sizeof(float4),
+                       cudaMemcpyDeviceToDevice, S(stream)));
+    ctx->snap_n[slot] = ctx->D.n;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_bgdo_default_options(mpm_bgdo_options *opt) {
+    if (!opt) return MPM_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->delta_target = 0.1f;
+    opt->w = -1.f;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_bgdo(mpm_ctx *ctx, int32_t n_keys, const int32_t *slots, const mpm_bgdo_options *opt,
+                            float *G, float *log_E, float *g_tau, float *delta, void *stream) {
+    if (!ctx) return MPM_ERR_INVALID_ARG;
+    if (n_keys < 1 || n_keys > MPM_MAX_SNAPSHOTS || !slots)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "n_keys must be in [1, MPM_MAX_SNAPSHOTS] with a slot list");
+    mpm_bgdo_options o;
+    mpm_bgdo_default_options(&o);
+    if (opt) o = *opt;
+    if (!std::isfinite(o.delta_target) || !(o.w <= 1.f) || (o.per_material & ~1) || (o.delta_pre_step & ~1))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "bgdo options: delta_target finite, w <= 1, flags 0 or 1");
+    if (o.per_material && 2 * ctx->table.size() * sizeof(double) > 48 * 1024)
+        return fail(ctx, MPM_ERR_INVALID_ARG, "too many materials for the per-material average");
+    if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state (load particles first)");
+    for (int k = 0; k < n_keys; ++k) {
+        const int sl = slots[k];
+        if (sl < 0 || sl >= MPM_MAX_SNAPSHOTS) return fail(ctx, MPM_ERR_INVALID_ARG, "snapshot slot out of range");
+        if (!ctx->snap[sl] || ctx->snap_n[sl] != ctx->D.n)
+            return fail(ctx, MPM_ERR_STATE, "slot " + std::to_string(sl) + " holds no snapshot of this particle count");
+    }
+    cudaStream_t st = S(stream);
+    Dev &D = ctx->D;
+    const size_t n = (size_t)D.n;
+    const int nm = (int)ctx->table.size();
+    mpm_status s;
+    if (ctx->bgdo_cap < ctx->cap) {
+        if ((s = dalloc(ctx, &ctx->bgdo_work, (size_t)ctx->cap * REC_F4, false))) return s;
+        if ((s = dalloc(ctx, &ctx->bgdo_G, (size_t)ctx->cap, false))) return s;
+        ctx->bgdo_cap = ctx->cap;
+    }
+    if (o.per_material && !ctx->bgdo_sum && (s = dalloc(ctx, &ctx->bgdo_sum, 2 * (size_t)nm, false))) return s;
+    // outputs: device pointers are written directly, host ones through the staging buffer
+    float *outs[4] = {G, log_E, g_tau, delta};
+    const size_t widths[4] = {1, 1, (size_t)n_keys, (size_t)n_keys};
+    float *dptr[4] = {nullptr, nullptr, nullptr, nullptr};
+    size_t offs[4] = {0, 0, 0, 0}, off = 0;
+    bool host_out = false;
+    for (int i = 0; i < 4; ++i) {
+        if (!outs[i]) continue;
+        if (is_device_ptr(outs[i])) { dptr[i] = outs[i]; continue; }
+        off = (off + 255) & ~size_t(255);
+        offs[i] = off;
+        off += n * widths[i] * sizeof(float);
+        host_out = true;
+    }
+    if (host_out) {
+        // the stream may still use the staging buffer: reallocate only after it drains
+        if (off > ctx->stage_bytes) CK(cudaStreamSynchronize(st));
+        if ((s = ensure_stage(ctx, off))) return s;
+        for (int i = 0; i < 4; ++i)
+            if (outs[i] && !dptr[i]) dptr[i] = (float *)((char *)ctx->stage + offs[i]);
+    }
+    const size_t rec_bytes = n * REC_F4 * sizeof(float4);
+    for (int k = 0; k < n_keys; ++k) {
+        const float4 *key = ctx->snap[slots[k]];
+        const float4 *post = key;
+        if (!o.delta_pre_step) {
+            // the pseudo substep: the ordinary substep on a copy of the key frame
+            CK(cudaMemcpyAsync(ctx->bgdo_work, key, rec_bytes, cudaMemcpyDeviceToDevice, st));
+            float4 *saved = D.rec;
+            D.rec = ctx->bgdo_work;
+            rebin(ctx, st);
+            s = run_substeps(ctx, 1, st);
+            D.rec = saved;
+            if (s) return s;
+            post = ctx->bgdo_work;
+        }
+        launch_bgdo_accum(D, key, post, k == 0, 1.f / (float)n_keys, o.delta_target, o.w, ctx->bgdo_G,
+                          dptr[2] ? dptr[2] + (size_t)k * n : nullptr, dptr[3] ? dptr[3] + (size_t)k * n : nullptr, st);
+        ++ctx->launches;
+        CKLAUNCH();
+    }
+    if (o.per_material) {
+        CK(cudaMemsetAsync(ctx->bgdo_sum, 0, 2 * (size_t)nm * sizeof(double), st));
+        launch_bgdo_material_sum(D, nm, ctx->bgdo_G, ctx->bgdo_sum, st);
+        ++ctx->launches;
+    }
+    if (dptr[0] || dptr[1]) {
+        launch_bgdo_finish(D, nm, ctx->bgdo_G, o.per_material ? ctx->bgdo_sum : nullptr, dptr[0], dptr[1], st);
+        ++ctx->launches;
+    }
+    CKLAUNCH();
+    if (!o.delta_pre_step) rebin(ctx, st);   // bins of the current state again
+    CKLAUNCH();
+    for (int i = 0; i < 4; ++i)
+        if (outs[i] && dptr[i] != outs[i])
+            CK(cudaMemcpyAsync(outs[i], dptr[i], n * widths[i] * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (host_out) return check_device_error(ctx, st);
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_load_covariance(mpm_ctx *ctx, const float *cov0, void *stream) {
+    if (!ctx || !cov0) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    const size_t n = (size_t)ctx->D.n;
+    mpm_status s;
+    if (ctx->cov_cap < ctx->cap) {
+        if ((s = dalloc(ctx, &ctx->cov0, (size_t)ctx->cap * 6, false))) return s;
+        ctx->cov_cap = ctx->cap;
+    }
+    CK(cudaMemcpyAsync(ctx->cov0, cov0, n * 6 * sizeof(float), cudaMemcpyDefault, S(stream)));
+    ctx->cov_n = ctx->D.n;
+    return MPM_OK;
+}
+
+MPM_API mpm_status mpm_get_covariance(mpm_ctx *ctx, float *cov, void *stream) {
+    if (!ctx || !cov) return MPM_ERR_INVALID_ARG;
+    if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    if (!ctx->cov0 || ctx->cov_n != ctx->D.n)
+        return fail(ctx, MPM_ERR_STATE, "no rest covariances loaded for this particle count");
+    cudaStream_t st = S(stream);
+    const size_t n = (size_t)ctx->D.n;
+    float *d = cov;
+    // the kernel stores float2: a device pointer off an 8-byte boundary goes through staging
+    if (!is_device_ptr(cov) || ((uintptr_t)cov & 7u)) {
+        if (n * 6 * sizeof(float) > ctx->stage_bytes) return fail(ctx, MPM_ERR_CUDA, "internal: staging too small");
+        d = (float *)ctx->stage;
+    }
+    launch_covariance(ctx->D, ctx->cov0, d, st);
+    ++ctx->launches;
+    CKLAUNCH();
+    if (d != cov) CK(cudaMemcpyAsync(cov, d, n * 6 * sizeof(float), cudaMemcpyDefault, st));
+    return MPM_OK;
+}
+
 MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream) {
     if (!ctx || !m || !mv) return MPM_ERR_INVALID_ARG;
     if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state");

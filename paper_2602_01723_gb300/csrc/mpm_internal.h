@@ -98,6 +98,17 @@ struct mpm_ctx {
     long long graph_key = -1;     // (n, buffer generation) the graph was captured for
     long long generation = 0;     // bumped whenever a device buffer the kernels use is reallocated
     bool bins_pending = false;    // a binning (counts / occupied list) awaits its plan
+    // BGDO key frames (records of the whole particle set) and stage-2 scratch
+    float4 *snap[MPM_MAX_SNAPSHOTS] = {};
+    long long snap_n[MPM_MAX_SNAPSHOTS] = {};     // particle count at the snapshot (0: empty)
+    long long snap_cap[MPM_MAX_SNAPSHOTS] = {};
+    float4 *bgdo_work = nullptr;   // pseudo-substep state
+    long long bgdo_cap = 0;
+    float *bgdo_G = nullptr;       // per-particle accumulator
+    double *bgdo_sum = nullptr;    // per-material sum and count (2 * n_materials)
+    // rest covariance of each particle's Gaussian kernel (n x 6)
+    float *cov0 = nullptr;
+    long long cov_n = 0, cov_cap = 0;
 };
 
 namespace mpm {
@@ -109,8 +120,16 @@ void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st);
 void L_prepare(mpm_ctx *ctx, int upd_par, int act_par, int do_sort, cudaStream_t st, int keep_momentum = 0);
 void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
 void L_bin(mpm_ctx *ctx, cudaStream_t st);
+void launch_bgdo_accum(const Dev &D, const float4 *key, const float4 *post, int first, float inv_k,
+                       float delta_target, float w, float *G, float *g_tau, float *delta, cudaStream_t st);
+void launch_bgdo_material_sum(const Dev &D, int n_mat, const float *G, double *sum, cudaStream_t st);
+void launch_bgdo_finish(const Dev &D, int n_mat, const float *G, const double *sum, float *Gout, float *logE,
+                        cudaStream_t st);
+void launch_covariance(const Dev &D, const float *cov0, float *out, cudaStream_t st);
 void launch_reduce_by_material(const Dev &D, int n_mat, const float *per_particle, float *out, cudaStream_t st);
 mpm_status ensure_chunks(mpm_ctx *ctx);
+// re-bins the records D.rec points at (after the bins of another state)
+void rebin(mpm_ctx *ctx, cudaStream_t st);
 mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape = nullptr, size_t tape_stride = 0);
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);

@@ -125,6 +125,37 @@ class Simulator:
         L.mpm_backward(self.ctx, list(frame_sub), _p(dL_dx), _p(g), _p(a0), _stream(stream))
         return (g, a0) if want_state0 else g
 
+    def load_covariance(self, cov0, stream=None):
+        """Rest covariance Sigma of each particle's Gaussian kernel, (n, 6)
+        xx xy xz yy yz zz (§3.1)."""
+        cov0 = _dev(cov0, torch.float32, self.device, 6)
+        L.mpm_load_covariance(self.ctx, _p(cov0), _stream(stream))
+        self._cov0 = cov0    # keep alive until the stream has copied it
+
+    def covariance(self, out=None, stream=None):
+        """Deformed covariance F Sigma F^T of every particle, (n, 6) (§3.2)."""
+        out = torch.empty((self.n, 6), device=self.device) if out is None else out
+        L.mpm_get_covariance(self.ctx, _p(out), _stream(stream))
+        return out
+
+    def snapshot(self, slot, stream=None):
+        """Stores the current state as BGDO key frame `slot` (Algorithm 1, Stage 1)."""
+        L.mpm_snapshot(self.ctx, slot, _stream(stream))
+
+    def bgdo(self, slots, delta_target=0.1, w=None, per_material=False, delta_pre_step=False, signals=False,
+             stream=None):
+        """BGDO stage 2 from the key frames in `slots` (§4.3, Algorithm 1,
+        App. F).  Returns the per-particle update G, the updated log E
+        (log E - G) and, with signals=True, the per-key g_tau and delta."""
+        n, K, dv = self.n, len(slots), self.device
+        out = {"G": torch.empty(n, device=dv), "log_E": torch.empty(n, device=dv)}
+        if signals:
+            out["g_tau"] = torch.empty((K, n), device=dv)
+            out["delta"] = torch.empty((K, n), device=dv)
+        L.mpm_bgdo(self.ctx, list(slots), delta_target, w, per_material, delta_pre_step, _p(out["G"]),
+                   _p(out["log_E"]), _p(out.get("g_tau")), _p(out.get("delta")), _stream(stream))
+        return out
+
     def debug_p2g(self, stream=None):
         nn = self.n_instances * self.grid_res[0] * self.grid_res[1] * self.grid_res[2]
         m = torch.empty(nn, device=self.device)

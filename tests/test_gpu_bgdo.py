@@ -1,0 +1,149 @@
+"""GPU parity of BGDO stage 2 (§4.3, Algorithm 1, App. F): libmpm's
+key-frame pseudo substep and per-particle signals against the FP64 oracle on
+the same seeded key frames.
+
+Tolerances, derived from the substep's own bounds: g_tau = |tau|_F is an FP32
+stress norm, within 1e-4 relative; delta = |F' - I|_F inherits the 2e-5
+per-entry bound on the post-step F (at most 3 x 2e-5 in the Frobenius norm);
+G = eta log(1 + g_tau) - (1 - eta)(delta - 0.1) then lies within
+1e-4 + 6e-5 < 2e-4 absolute."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_01723_gb300 import scenes  # noqa: E402
+
+GT_RTOL = 1e-4
+DELTA_TOL = 6e-5
+G_TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def sim_mod():
+    from __graft_entry__ import build
+    build()
+    from paper_2602_01723_gb300 import sim
+    return sim
+
+
+def mixed_cube():
+    sc = scenes.cube_8k()
+    sc.materials = [scenes.material(0, 0, 1e4, 0.3, 10.0), scenes.material(1, 0, 2e4, 0.3, 10.0),
+                    scenes.material(0, 1, 1e4, 0.3, 10.0, yield_stress=50.0), scenes.material(0, 2, 3e3, 0.25, 10.0)]
+    sc.mat_id = (np.arange(sc.n) % 4).astype(np.int32)
+    return sc
+
+
+def gpu_bgdo(sim_mod, sc, keys, **opt):
+    s = sim_mod.Simulator.from_scene(sc)
+    for k, (v, C, F) in enumerate(keys):
+        s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F, instance=sc.instance, params=sc.params)
+        s.snapshot(k)
+    out = s.bgdo(list(range(len(keys))), signals=True, **opt)
+    s.sync()
+    s.close()
+    return {k: t.double().cpu().numpy() for k, t in out.items()}
+
+
+def oracle_bgdo(orc, sc, keys, **opt):
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
+    states = [orc.new_state(sc.x, v, C, F) for v, C, F in keys]
+    return orc.bgdo(cfg, states, mat, label=sc.mat_id, **opt)
+
+
+def compare(got, ref):
+    gt_scale = np.abs(ref["g_tau"]).max()
+    assert np.all(np.abs(got["g_tau"] - ref["g_tau"]) <= GT_RTOL * np.abs(ref["g_tau"]) + 1e-6 * gt_scale)
+    assert np.abs(got["delta"] - ref["delta"]).max() < DELTA_TOL
+    assert np.abs(got["G"] - ref["G"]).max() < G_TOL
+    assert np.abs(got["log_E"] - ref["log_E"]).max() < G_TOL + 1e-5
+
+
+def test_bgdo_three_keys_all_models(orc, sim_mod):
+    sc = mixed_cube()
+    keys = scenes.key_frames(sc, 3)
+    compare(gpu_bgdo(sim_mod, sc, keys), oracle_bgdo(orc, sc, keys))
+
+
+@pytest.mark.parametrize("opt", [dict(w=0.3), dict(per_material=True), dict(delta_pre_step=True),
+                                 dict(delta_target=0.05, w=1.0)])
+def test_bgdo_options(orc, sim_mod, opt):
+    sc = mixed_cube()
+    keys = scenes.key_frames(sc, 2, k_seed=41)
+    compare(gpu_bgdo(sim_mod, sc, keys, **opt), oracle_bgdo(orc, sc, keys, **opt))
+
+
+def test_bgdo_full_size_three_objects(orc, sim_mod):
+    """The 300k-particle three-object scene (128^3 grid) at full size: every
+    particle's G against the oracle."""
+    sc = scenes.three_objects_300k()
+    keys = scenes.key_frames(sc, 3, k_seed=42, cs=2.0, fs=0.03)
+    compare(gpu_bgdo(sim_mod, sc, keys), oracle_bgdo(orc, sc, keys))
+
+
+def test_bgdo_iteration_from_a_forward_run(orc, sim_mod):
+    """Algorithm 1 end to end on the 512-particle ball: stage 1 forward with
+    key frames at substeps 0, 40, 80 on each side, then stage 2."""
+    sc = scenes.ball_512()
+    sc.params = None
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.snapshot(0)
+    s.step(40)
+    s.snapshot(1)
+    s.step(40)
+    s.snapshot(2)
+    got = {k: t.double().cpu().numpy() for k, t in s.bgdo([0, 1, 2], signals=True).items()}
+    s.close()
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials)
+    s0 = orc.new_state(sc.x, sc.v)
+    s1 = orc.run(cfg, s0, mat, 40)
+    s2 = orc.run(cfg, s1, mat, 40)
+    compare(got, orc.bgdo(cfg, [s0, s1, s2], mat))
+
+
+def test_bgdo_leaves_the_state_and_its_continuation_unchanged(sim_mod):
+    sc = scenes.cube_8k()
+    v, C, F = scenes.key_frames(sc, 1)[0]
+    runs = []
+    for with_bgdo in (False, True):
+        s = sim_mod.Simulator.from_scene(sc)
+        s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+        s.step(5)
+        before = {k: t.clone() for k, t in s.get().items()}
+        if with_bgdo:
+            s.snapshot(3)
+            s.step(2)
+            s.bgdo([3])
+            s.sync()
+        else:
+            s.step(2)
+        mid = s.get()
+        s.step(10)
+        s.sync()
+        runs.append((before, mid, s.get()))
+        s.close()
+    for k in ("x", "v", "C", "F"):
+        assert torch.equal(runs[0][0][k], runs[1][0][k])
+        assert torch.equal(runs[0][1][k], runs[1][1][k])
+    assert (runs[0][2]["x"] - runs[1][2]["x"]).abs().max().item() < 1e-6 * sc.dx
+
+
+def test_bgdo_rejects_empty_and_stale_slots(sim_mod):
+    from paper_2602_01723_gb300._lib import MpmError
+    sc = scenes.ball_512()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    with pytest.raises(MpmError):
+        s.bgdo([5])
+    s.snapshot(0)
+    s.load(sc.x[:100], sc.vol[:100], sc.mat_id[:100])
+    with pytest.raises(MpmError):
+        s.bgdo([0])
+    with pytest.raises(MpmError):
+        s.bgdo([])
+    s.close()
