@@ -20,6 +20,9 @@
  *   - Lame parameters from (E, nu) (App. B.1);
  *   - von Mises and Drucker-Prager return maps on log singular values
  *     (App. A, eq. von_mises and eq. drucker_prager; App. B.2);
+ *   - the further models of App. B.1 (StVK with Green strain, Hencky /
+ *     SigmaElasticity, FluidElasticity, VolumeElasticity) and the
+ *     volume-only plasticity of App. A (fluid) and App. B.2 (Sigma);
  *   - BGDO stage 2: key-frame pseudo step, stress-norm gradient in log E,
  *     log compression and Frobenius deformation guidance (§4.3, Algorithm 1,
  *     App. F);
@@ -58,8 +61,8 @@ typedef struct {
     const double *nu;        /* Poisson ratio */
     const double *yield;     /* von Mises yield stress sigma_y */
     const double *phi_deg;   /* Drucker-Prager friction angle, degrees */
-    const int *elastic;      /* 0 fixed-corotated, 1 Neo-Hookean */
-    const int *plastic;      /* 0 identity, 1 von Mises, 2 Drucker-Prager */
+    const int *elastic;      /* 0 fixed-corotated, 1 Neo-Hookean, 2 StVK, 3 Hencky, 4 fluid, 5 volume */
+    const int *plastic;      /* 0 identity, 1 von Mises, 2 Drucker-Prager, 3 fluid, 4 Sigma */
 } orc_material;
 
 enum { ORC_OK = 0, ORC_OUT_OF_DOMAIN = 1, ORC_NONFINITE = 2 };
@@ -302,8 +305,53 @@ void orc_polar(const double F[9], double R[9]) {
 /*                tau = mu (F F^T - I) + lambda log J I                        */
 /* ------------------------------------------------------------------------ */
 
+/* Further elastic models of App. B.1 (model codes 2..5):
+ *   2 StVK, Green strain E = (F^T F - I)/2: the App. B.1 expression read as a
+ *     first Piola-Kirchhoff stress P = 2 mu F E + lambda J (J - 1) F^{-T}, so
+ *     tau = P F^T = 2 mu F E F^T + lambda J (J - 1) I;
+ *   3 Hencky / SigmaElasticity, eps = log Sigma:
+ *     tau = U diag(2 mu eps + lambda tr(eps)) U^T (the same tau as App. A's
+ *     StVK, whose P = U (2 mu Sigma^{-1} log Sigma + lambda tr(log Sigma)
+ *     Sigma^{-1}) V^T gives P F^T = this); singular values are floored at
+ *     1e-4 before the log, as in the return maps;
+ *   4 FluidElasticity: tau = lambda J (J - 1) I;
+ *   5 VolumeElasticity: tau = kappa (J - J^{1 - gamma}) I, kappa =
+ *     2 mu / 3 + lambda, gamma = 2 (J <= 0 is non-finite).                  */
 int orc_kirchhoff(int model, const double F[9], double mu, double lam, double tau[9]) {
     double J = m_det(F);
+    if (model == 2) {
+        double E[9], FE[9];
+        m_mul_tn(E, F, F);
+        for (int i = 0; i < 9; ++i) E[i] *= 0.5;
+        E[0] -= 0.5; E[4] -= 0.5; E[8] -= 0.5;
+        m_mul(FE, F, E);
+        m_mul_nt(tau, FE, F);
+        for (int i = 0; i < 9; ++i) tau[i] *= 2.0 * mu;
+        double vol = lam * J * (J - 1.0);
+        tau[0] += vol; tau[4] += vol; tau[8] += vol;
+        return ORC_OK;
+    }
+    if (model == 3) {
+        double U[9], S[3], V[9], eps[3], d[3];
+        orc_svd(F, U, S, V);
+        double tr = 0.0;
+        for (int i = 0; i < 3; ++i) { eps[i] = log(S[i] > SIGMA_FLOOR ? S[i] : SIGMA_FLOOR); tr += eps[i]; }
+        for (int i = 0; i < 3; ++i) d[i] = 2.0 * mu * eps[i] + lam * tr;
+        usvt(tau, U, d, U);
+        return ORC_OK;
+    }
+    if (model == 4) {
+        memset(tau, 0, 9 * sizeof(double));
+        tau[0] = tau[4] = tau[8] = lam * J * (J - 1.0);
+        return ORC_OK;
+    }
+    if (model == 5) {
+        if (!(J > 0.0)) return ORC_NONFINITE;
+        double kappa = 2.0 * mu / 3.0 + lam;
+        memset(tau, 0, 9 * sizeof(double));
+        tau[0] = tau[4] = tau[8] = kappa * (J - 1.0 / J);
+        return ORC_OK;
+    }
     if (model == 0) {
         double R[9], M[9];
         orc_polar(F, R);
@@ -364,9 +412,21 @@ static int return_map_sigma(int model, const double s[3], double mu, double lam,
     return PM_PROJECT;
 }
 
+/* Volume-only plasticity (model codes 3, 4):
+ *   3 fluid (App. A eq. fluid_plasticity): F <- J^{1/3} I;
+ *   4 SigmaPlasticity (App. B.2): J clamped to [0.05, 1.2], F <- J^{1/3} I.
+ * cbrt keeps the sign of J, so an inverted F stays inverted under (3).      */
 int orc_return_map(int model, const double F[9], double mu, double lam, double yield, double phi_deg,
                    double Fout[9]) {
     if (model == 0) { m_copy(Fout, F); return PM_ELASTIC; }
+    if (model == 3 || model == 4) {
+        double J = m_det(F);
+        if (model == 4) J = J < 0.05 ? 0.05 : (J > 1.2 ? 1.2 : J);
+        double c = cbrt(J);
+        memset(Fout, 0, 9 * sizeof(double));
+        Fout[0] = Fout[4] = Fout[8] = c;
+        return PM_PROJECT;
+    }
     double U[9], S[3], V[9], z[3];
     orc_svd(F, U, S, V);
     int c = return_map_sigma(model, S, mu, lam, yield, phi_deg, z);
@@ -568,12 +628,99 @@ static void polar_adjoint(const double U[9], const double S[3], const double V[9
     for (int i = 0; i < 9; ++i) Fbar[i] += D[i];
 }
 
+/* (log a - log b) / (a - b) for a, b > 0; 1/a at a = b */
+static double log_divdiff(double a, double b) {
+    double d = a - b;
+    if (fabs(d) <= 1e-6 * (a + b)) return 2.0 / (a + b);
+    return (log(a) - log(b)) / d;
+}
+
 /* adjoint of the Kirchhoff stress; adds to Fbar, mubar, lambar */
 static void kirchhoff_adjoint(int model, const double F[9], double mu, double lam, const double taubar[9],
                               double Fbar[9], double *mubar, double *lambar) {
     double J = m_det(F), cof[9];
     m_cofactor(cof, F);                  /* dJ/dF */
     double trb = m_trace(taubar);
+    if (model == 2) {
+        /* tau = 2 mu F E F^T + lam J (J-1) I, E = (F^T F - I)/2:
+         * d<tb, F E F^T> = <tb F E + tb^T F E + F (B + B^T)/2, dF>, B = F^T tb F */
+        double E[9], FE[9], A[9], B[9], T[9], X[9];
+        m_mul_tn(E, F, F);
+        for (int i = 0; i < 9; ++i) E[i] *= 0.5;
+        E[0] -= 0.5; E[4] -= 0.5; E[8] -= 0.5;
+        m_mul(FE, F, E);
+        m_mul_nt(A, FE, F);
+        *mubar += 2.0 * m_dot(taubar, A);
+        *lambar += trb * J * (J - 1.0);
+        m_mul_tn(T, F, taubar);
+        m_mul(B, T, F);
+        double Bs[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) Bs[3 * i + j] = 0.5 * (B[3 * i + j] + B[3 * j + i]);
+        double tbs[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) tbs[3 * i + j] = taubar[3 * i + j] + taubar[3 * j + i];
+        m_mul(X, tbs, FE);
+        m_mul(T, F, Bs);
+        for (int i = 0; i < 9; ++i) X[i] += T[i];
+        double Jbar = lam * trb * (2.0 * J - 1.0);
+        for (int i = 0; i < 9; ++i) Fbar[i] += 2.0 * mu * X[i] + Jbar * cof[i];
+        return;
+    }
+    if (model == 3) {
+        /* tau = h(b), b = F F^T = U diag(beta) U^T, h_i = 2 mu eps_i + lam tr eps,
+         * eps_i = log(max(sigma_i, floor)).  With K = U^T sym(taubar) U:
+         * bbar~_kk = sum_i K_ii dh_i/dbeta_k, bbar~_ij = K_ij (h_i - h_j)/(beta_i - beta_j),
+         * Fbar += (bbar + bbar^T) F. */
+        double U[9], S[3], V[9], eps[3], live[3], beta[3], tr = 0.0;
+        orc_svd(F, U, S, V);
+        for (int i = 0; i < 3; ++i) {
+            live[i] = S[i] > SIGMA_FLOOR ? 1.0 : 0.0;
+            eps[i] = log(live[i] > 0.0 ? S[i] : SIGMA_FLOOR);
+            beta[i] = S[i] * S[i];
+            tr += eps[i];
+        }
+        double tbs[9], T[9], K[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) tbs[3 * i + j] = 0.5 * (taubar[3 * i + j] + taubar[3 * j + i]);
+        m_mul_tn(T, U, tbs);
+        m_mul(K, T, U);
+        double trK = K[0] + K[4] + K[8];
+        for (int i = 0; i < 3; ++i) *mubar += 2.0 * K[4 * i] * eps[i];
+        *lambar += trK * tr;
+        double Bt[9];
+        m_zero(Bt);
+        for (int k = 0; k < 3; ++k)   /* d eps_k / d beta_k = 1 / (2 beta_k) */
+            Bt[4 * k] = live[k] * (2.0 * mu * K[4 * k] + lam * trK) / (2.0 * beta[k]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (i == j) continue;
+                double dd = (live[i] > 0.0 && live[j] > 0.0) ? mu * log_divdiff(beta[i], beta[j]) : 0.0;
+                Bt[3 * i + j] = K[3 * i + j] * dd;      /* 2 mu (eps_i - eps_j)/(beta_i - beta_j) */
+            }
+        double Bb[9], D[9];
+        m_mul(T, U, Bt);
+        m_mul_nt(Bb, T, U);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) D[3 * i + j] = Bb[3 * i + j] + Bb[3 * j + i];
+        m_mul(T, D, F);
+        for (int i = 0; i < 9; ++i) Fbar[i] += T[i];
+        return;
+    }
+    if (model == 4) {
+        *lambar += trb * J * (J - 1.0);
+        double Jbar = lam * trb * (2.0 * J - 1.0);
+        for (int i = 0; i < 9; ++i) Fbar[i] += Jbar * cof[i];
+        return;
+    }
+    if (model == 5) {
+        double kappa = 2.0 * mu / 3.0 + lam, kbar = trb * (J - 1.0 / J);
+        *mubar += 2.0 / 3.0 * kbar;
+        *lambar += kbar;
+        double Jbar = kappa * trb * (1.0 + 1.0 / (J * J));
+        for (int i = 0; i < 9; ++i) Fbar[i] += Jbar * cof[i];
+        return;
+    }
     if (model == 0) {
         double U[9], S[3], V[9], R[9], M[9], T[9];
         orc_svd(F, U, S, V);
@@ -666,6 +813,16 @@ static int return_map_jacobian(int model, const double s[3], double mu, double l
 static void plastic_adjoint(int model, const double G[9], double mu, double lam, double yield, double phi_deg,
                             const double Fbar_out[9], double Gbar[9], double *mubar, double *lambar, double *ybar) {
     if (model == 0) { m_copy(Gbar, Fbar_out); return; }
+    if (model == 3 || model == 4) {
+        /* F = c I, c = J^{1/3} (clamped J for model 4, where a clamp stops the
+         * derivative): dc = (c / 3J) dJ, dJ = <cof G, dG> */
+        double J = m_det(G), cof[9];
+        m_cofactor(cof, G);
+        int clamped = model == 4 && (J < 0.05 || J > 1.2);
+        double c = cbrt(J), k = clamped ? 0.0 : m_trace(Fbar_out) * c / (3.0 * J);
+        for (int i = 0; i < 9; ++i) Gbar[i] = k * cof[i];
+        return;
+    }
     double U[9], S[3], V[9], z[3], Jz[9], dmu[3], dlam[3], dy[3];
     orc_svd(G, U, S, V);
     int c = return_map_jacobian(model, S, mu, lam, yield, phi_deg, z, Jz, dmu, dlam, dy);

@@ -32,7 +32,10 @@ def objective(orc, cfg, st, mat, c):
     return float(np.sum(orc.pack(orc.substep(cfg, st, mat)) * c))
 
 
-@pytest.mark.parametrize("model", [(0, 0), (1, 0), (0, 1), (0, 2)], ids=["fcr", "nh", "fcr_vm", "fcr_dp"])
+@pytest.mark.parametrize("model", [(0, 0), (1, 0), (0, 1), (0, 2), (2, 0), (3, 0), (4, 0), (5, 0), (0, 3), (0, 4),
+                                   (3, 2), (4, 3)],
+                         ids=["fcr", "nh", "fcr_vm", "fcr_dp", "stvk", "hencky", "fluid", "volume", "fcr_fluidplastic",
+                              "fcr_sigmaplastic", "hencky_dp", "fluid_fluidplastic"])
 def test_substep_adjoint_matches_central_differences(orc, model):
     cfg, st, mat, rng = setup_case(orc, model, seed=sum(model) * 7 + model[0])
     n = len(st["x"])
@@ -59,9 +62,12 @@ def test_substep_adjoint_matches_central_differences(orc, model):
             err = abs(fd - adj_in[p, k]) / (abs(fd) + 1e-3 * np.abs(adj_in).max() + 1e-30)
             worst = max(worst, err)
     assert worst < 2e-5
+    # central-difference roundoff: about eps |f| / h per evaluation pair
+    f0 = abs(objective(orc, cfg, st, mat, c))
     for j, attr in enumerate(["logE", "nu", "yield_stress"]):
         for p in range(n):
             h = 1e-6
+            fd_floor = 8 * np.finfo(float).eps * f0 / h
             a = getattr(mat, attr).copy()
             ap, am = a.copy(), a.copy()
             ap[p] += h
@@ -69,7 +75,8 @@ def test_substep_adjoint_matches_central_differences(orc, model):
             fp = objective(orc, cfg, st, mat.with_params(**{attr: ap}), c)
             fm = objective(orc, cfg, st, mat.with_params(**{attr: am}), c)
             fd = (fp - fm) / (2 * h)
-            assert abs(fd - g[p, j]) <= 2e-5 * (abs(fd) + 1e-3 * np.abs(g[:, j]).max()) + 1e-12, (attr, p, fd, g[p, j])
+            assert abs(fd - g[p, j]) <= 2e-5 * (abs(fd) + 1e-3 * np.abs(g[:, j]).max()) + fd_floor + 1e-12, \
+                (attr, p, fd, g[p, j])
 
 
 def test_yield_gradient_is_nonzero_only_for_plastic_particles(orc):
