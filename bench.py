@@ -148,9 +148,9 @@ def oracle_rate(sc, n_sub):
     mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
     st = orc.new_state(sc.x, sc.v)
     t0 = time.perf_counter()
-    orc.run(cfg, st, mat, n_sub)
+    out = orc.run(cfg, st, mat, n_sub)
     t = time.perf_counter() - t0
-    return sc.n * n_sub / t, t
+    return sc.n * n_sub / t, t, out
 
 
 def run_reference(args):
@@ -287,35 +287,36 @@ def run_ours(args):
     h2d = n * (12 + 12 + 4 + 4)
     d2h = n * 12
 
-    # error against the FP64 oracle: one teacher-forced substep from the GPU
-    # state after the full run (grid momentum over all nodes, positions on a
-    # 4,000-particle sample)
+    # error against the FP64 oracle, both sides from the same seeded inputs:
+    # (1) the P2G grid (all nodes) of a stressed key frame of the scene;
+    # (2) positions after the oracle's timed sample of free-running substeps
+    #     from the scene's start (the CPU baseline run below)
     err = {}
+    cpu = None
     if rank == 0:
         import oracle as orc
-        st = {k: v.double().cpu().numpy() for k, v in sim.get().items()}
-        m, mv = sim.debug_p2g()
         cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
         mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
-        ost = orc.new_state(st["x"], st["v"], st["C"], st["F"])
-        gm, gmv = orc.p2g(cfg, ost, mat)
+        kv, kC, kF = scenes.key_frames(sc, 1, k_seed=46, vs=0.5, cs=2.0, fs=0.1)[0]
+        sim.load(sc.x, sc.vol, sc.mat_id, v=kv, C=kC, F=kF)
+        m, mv = sim.debug_p2g()
+        gm, gmv = orc.p2g(cfg, orc.new_state(sc.x, kv, kC, kF), mat)
         floor = np.abs(gm).max() * 9.8 * sc.dt
         err["grid_m_rel"] = float(np.abs(m[0].double().cpu().numpy() - gm).max() / max(np.abs(gm).max(), floor))
         err["grid_mv_rel"] = float(np.abs(mv[0].double().cpu().numpy() - gmv).max() / max(np.abs(gmv).max(), floor))
-        sim.step(1)
-        got = sim.get()["x"].double().cpu().numpy()
-        gv = orc.grid_update(cfg, gm, gmv)
-        idx = np.random.default_rng(0).choice(n, 4000, replace=False)
-        sub = orc.new_state(st["x"][idx], st["v"][idx], st["C"][idx], st["F"][idx])
-        ref = orc.g2p(cfg, sub, mat.subset(idx), gv)
-        err["x_one_substep_max_dx"] = float(np.abs(got[idx] - ref["x"]).max() / sc.dx)
-        err["note"] = "teacher-forced: FP32 GPU vs FP64 oracle from the same state after %d substeps" % S
+        cpu = oracle_rate(sc, ORACLE_SAMPLE_SUBSTEPS)
+        sim.load_scene(sc)
+        sim.step(ORACLE_SAMPLE_SUBSTEPS)
+        xg = sim.positions().double().cpu().numpy()
+        err["x_after_%d_substeps_max_dx" % ORACLE_SAMPLE_SUBSTEPS] = float(np.abs(xg - cpu[2]["x"]).max() / sc.dx)
+        err["note"] = ("FP32 GPU vs FP64 oracle from the same seeded inputs: P2G of a stressed key frame, and "
+                       "free-running positions after %d substeps" % ORACLE_SAMPLE_SUBSTEPS)
 
     fb = fwd_bwd(args, dev, flush, world, dist)
     bg = bgdo_leg(args, sim, sc, (x0, v0, vol, mid), flush)
 
     if rank == 0:
-        cpu_v, cpu_t = oracle_rate(sc, ORACLE_SAMPLE_SUBSTEPS)
+        cpu_v, cpu_t = cpu[0], cpu[1]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,

@@ -215,6 +215,118 @@ __device__ void nh_adjoint(const float F[9], float mu, float lam, const float T[
     lambar += trT * log1pf(jm1);
 }
 
+// Reverse of the further elastic models (out of line, like their forward):
+//   StVK:   Fbar += 2 mu (2 T F E + F B) + lam tr(T)(2J - 1) cof F,  B = F^T T F,
+//           mubar += 2 <T, F E F^T>, lambar += tr(T) J (J - 1)
+//   Hencky: in the singular basis, with K = U^T T U and eps = log s:
+//           Z_kk = (2 mu K_kk + lam tr K) / s_k,
+//           Z_ij = 4 mu K_ij s_j (eps_i - eps_j) / (s_i^2 - s_j^2)   (i != j),
+//           Fbar += U Z V^T, mubar += 2 sum K_ii eps_i, lambar += tr K tr eps
+//           (floored singular values carry no derivative)
+//   fluid:  Fbar += lam tr(T)(2J - 1) cof F, lambar += tr(T) J (J - 1)
+//   volume: kappabar = tr(T)(J - 1/J): mubar += 2/3 kappabar, lambar += kappabar,
+//           Fbar += kappa tr(T)(1 + 1/J^2) cof F
+static __device__ __noinline__ void more_adjoint(int elastic, const float *F, const float *U, const float *V, const float *s,
+                                          const float *e, float mu, float lam, const float *T, float *Fbar,
+                                          float *mubar, float *lambar) {
+    const float trT = T[0] + T[4] + T[8];
+    const float jm1 = det_minus_one(F);
+    const float J = 1.f + jm1;
+    const float cof[9] = {F[4] * F[8] - F[5] * F[7], F[5] * F[6] - F[3] * F[8], F[3] * F[7] - F[4] * F[6],
+                          F[2] * F[7] - F[1] * F[8], F[0] * F[8] - F[2] * F[6], F[1] * F[6] - F[0] * F[7],
+                          F[1] * F[5] - F[2] * F[4], F[2] * F[3] - F[0] * F[5], F[0] * F[4] - F[1] * F[3]};
+    if (elastic == ELASTIC_STVK) {
+        float h[9];
+        for (int i = 0; i < 9; ++i) h[i] = F[i];
+        h[0] -= 1.f; h[4] -= 1.f; h[8] -= 1.f;
+        float E[9], FE[9], TF[9], B[9], A[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                E[3 * i + j] = 0.5f * (h[3 * i + j] + h[3 * j + i] + h[i] * h[j] + h[3 + i] * h[3 + j] +
+                                       h[6 + i] * h[6 + j]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                FE[3 * i + j] = F[3 * i] * E[j] + F[3 * i + 1] * E[3 + j] + F[3 * i + 2] * E[6 + j];
+                TF[3 * i + j] = T[3 * i] * F[j] + T[3 * i + 1] * F[3 + j] + T[3 * i + 2] * F[6 + j];
+            }
+        float acc = 0.f;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                // B = F^T (T F), A = F E F^T
+                B[3 * i + j] = F[i] * TF[j] + F[3 + i] * TF[3 + j] + F[6 + i] * TF[6 + j];
+                A[3 * i + j] = FE[3 * i] * F[3 * j] + FE[3 * i + 1] * F[3 * j + 1] + FE[3 * i + 2] * F[3 * j + 2];
+                acc += T[3 * i + j] * A[3 * i + j];
+            }
+        const float Jbar = lam * trT * (2.f * J - 1.f);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                const float tfe = T[3 * i] * FE[j] + T[3 * i + 1] * FE[3 + j] + T[3 * i + 2] * FE[6 + j];
+                const float fb = F[3 * i] * B[j] + F[3 * i + 1] * B[3 + j] + F[3 * i + 2] * B[6 + j];
+                Fbar[3 * i + j] += 2.f * mu * (2.f * tfe + fb) + Jbar * cof[3 * i + j];
+            }
+        *mubar += 2.f * acc;
+        *lambar += trT * J * jm1;
+    } else if (elastic == ELASTIC_HENCKY) {
+        float K[9];
+        ut_m_v(K, U, T, U);
+        float eps[3];
+        bool live[3];
+        for (int i = 0; i < 3; ++i) {
+            live[i] = s[i] > MPM_SIGMA_FLOOR;
+            eps[i] = live[i] ? log1pf(e[i]) : -9.210340371976184f;
+        }
+        const float trK = K[0] + K[4] + K[8], tre = eps[0] + eps[1] + eps[2];
+        float Z[9];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                if (i == j) {
+                    Z[4 * i] = live[i] ? (2.f * mu * K[4 * i] + lam * trK) / s[i] : 0.f;
+                    continue;
+                }
+                float q;   // (eps_i - eps_j) / (s_i - s_j)
+                const float ds = s[i] - s[j];
+                if (live[i] && live[j]) {
+                    const float r = ds / s[j];
+                    q = fabsf(r) < 1e-3f ? (1.f - 0.5f * r + r * r * (1.f / 3.f)) / s[j] : log1pf(r) / ds;
+                } else {
+                    q = ds != 0.f ? (eps[i] - eps[j]) / ds : 0.f;
+                }
+                const float ss = s[i] + s[j];
+                Z[3 * i + j] = ss != 0.f ? 4.f * mu * K[3 * i + j] * s[j] * q / ss : 0.f;
+            }
+        float D[9];
+        u_z_vt(D, U, Z, V);
+        for (int t = 0; t < 9; ++t) Fbar[t] += D[t];
+        *mubar += 2.f * (K[0] * eps[0] + K[4] * eps[1] + K[8] * eps[2]);
+        *lambar += trK * tre;
+    } else if (elastic == ELASTIC_FLUID) {
+        const float Jbar = lam * trT * (2.f * J - 1.f);
+        for (int t = 0; t < 9; ++t) Fbar[t] += Jbar * cof[t];
+        *lambar += trT * J * jm1;
+    } else if (elastic == ELASTIC_VOLUME) {
+        const float kappa = 2.f * mu / 3.f + lam, kb = trT * jm1 * (2.f + jm1) / J;
+        *mubar += (2.f / 3.f) * kb;
+        *lambar += kb;
+        const float Jbar = kappa * trT * (1.f + 1.f / (J * J));
+        for (int t = 0; t < 9; ++t) Fbar[t] += Jbar * cof[t];
+    }
+}
+
+// Reverse of the volume-only plasticity F = c I, c = J^{1/3} (J clamped for
+// Sigma, where a clamp stops the derivative): Gbar = tr(Fbar) c / (3 J) cof G
+static __device__ __noinline__ void volume_plastic_adjoint(int plastic, const float *G, const float *Fbar, float *Gbar) {
+    float jm1 = det_minus_one(G);
+    const bool clamped = plastic == PLASTIC_SIGMA && (jm1 < 0.05f - 1.f || jm1 > 1.2f - 1.f);
+    const float J = 1.f + jm1;
+    const float c = J > 0.f ? expf(log1pf(jm1) * (1.f / 3.f)) : cbrtf(J);
+    const float k = clamped ? 0.f : (Fbar[0] + Fbar[4] + Fbar[8]) * c / (3.f * J);
+    Gbar[0] = k * (G[4] * G[8] - G[5] * G[7]); Gbar[1] = k * (G[5] * G[6] - G[3] * G[8]);
+    Gbar[2] = k * (G[3] * G[7] - G[4] * G[6]); Gbar[3] = k * (G[2] * G[7] - G[1] * G[8]);
+    Gbar[4] = k * (G[0] * G[8] - G[2] * G[6]); Gbar[5] = k * (G[1] * G[6] - G[0] * G[7]);
+    Gbar[6] = k * (G[1] * G[5] - G[2] * G[4]); Gbar[7] = k * (G[2] * G[3] - G[0] * G[5]);
+    Gbar[8] = k * (G[0] * G[4] - G[1] * G[3]);
+}
+
 // (mubar, lambar) -> (d/d log E, d/d nu), with E and nu recovered from mu, lambda
 __device__ __forceinline__ void lame_chain(float mu, float lam, float mubar, float lambar, float &gE, float &gnu) {
     const float nu = lam / (2.f * (lam + mu));
@@ -388,7 +500,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
 #pragma unroll
             for (int t = 0; t < 9; ++t) Gb[t] = Fb[t];
             float mubar = 0.f, lambar = 0.f, ybar = 0.f;
-            if (P.plastic != PLASTIC_NONE) {
+            if (P.plastic >= PLASTIC_FLUID) {
+                volume_plastic_adjoint(P.plastic, G, Fb, Gb);
+            } else if (P.plastic != PLASTIC_NONE) {
                 float U[9], V[9], s3[3], e3[3], d3[3], z[3], ze[3];
                 svd3_robust(G, U, V, s3, e3, d3);
                 const int rm = return_map(P.plastic, s3, e3, d3, P.mu, P.lam, P.yield, P.alpha, z, ze);
@@ -588,12 +702,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
             // recompute the stress and the affine momentum A = m C - k tau
             float U[9], V[9], s3[3], e3[3], d3[3];
             Sym tau;
-            if (P.elastic == 0) {
-                svd3_robust(P.F, U, V, s3, e3, d3);
-                tau = tau_fcr(U, s3, e3, P.mu, P.lam);
-            } else if (!tau_nh(P.F, P.mu, P.lam, tau)) {
-                tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            }
+            if (elastic_needs_svd(P.elastic)) svd3_robust(P.F, U, V, s3, e3, d3);
+            if (!kirchhoff(P.elastic, P.F, U, s3, e3, P.mu, P.lam, tau)) tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             const float kf = 4.f * dt * P.vol * inv_dx * inv_dx;
             const float A[9] = {P.mass * P.C[0] - kf * tau.xx, P.mass * P.C[1] - kf * tau.xy,
                                 P.mass * P.C[2] - kf * tau.xz, P.mass * P.C[3] - kf * tau.xy,
@@ -634,8 +744,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
                 for (int cc = 0; cc < 3; ++cc) T[3 * r + cc] = -0.5f * kf * (Ab[3 * r + cc] + Ab[3 * cc + r]);
             float Fb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             float mubar = 0.f, lambar = 0.f;
-            if (P.elastic == 0) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
-            else nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
+            if (P.elastic == ELASTIC_FCR) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
+            else if (P.elastic == ELASTIC_NH) nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
+            else more_adjoint(P.elastic, P.F, U, V, s3, e3, P.mu, P.lam, T, Fb, &mubar, &lambar);
             float4 *op = aout + (size_t)p * ADJ_F4;
             const float4 o0 = op[0], o3 = op[3], o4 = op[4], o5 = op[5];
             op[0] = make_float4(o0.x + xa[0], o0.y + xa[1], o0.z + xa[2], va[0]);

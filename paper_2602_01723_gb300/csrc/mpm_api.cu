@@ -358,7 +358,7 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
         if (o.walls[i] < 0 || o.walls[i] > 2) { g_create_error = "bad wall type"; return MPM_ERR_INVALID_ARG; }
     for (int m = 0; m < n_materials; ++m) {
         const mpm_material &t = table[m];
-        if (t.elastic < 0 || t.elastic > 1 || t.plastic < 0 || t.plastic > 2 || !(t.E > 0.f) || !(t.rho > 0.f) ||
+        if (t.elastic < 0 || t.elastic > 5 || t.plastic < 0 || t.plastic > 4 || !(t.E > 0.f) || !(t.rho > 0.f) ||
             !(t.nu > -1.f && t.nu < 0.5f)) {
             g_create_error = "bad material table entry";
             return MPM_ERR_INVALID_ARG;
@@ -434,8 +434,11 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     CREATE_TRY(dalloc(ctx, &D.ctr, CTR_COUNT, true));
     CREATE_TRY(dalloc(ctx, &D.err, 1, true));
     D.scatter = o.scatter;
+    D.xm = 0;
+    for (int m = 0; m < n_materials; ++m)
+        if (el[m] > 1 || pl[m] > 2) D.xm = 1;   // further models: the XM kernel variant
     for (int m = 0; m < 3; ++m) {
-        int occ = substep_occupancy(m, D.scatter, D.chunk);
+        int occ = substep_occupancy(m, D.scatter, D.chunk, D.xm != 0);
         ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->grid_small = ctx->sm_count * 8;
@@ -639,7 +642,7 @@ MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, 
     if (s) { D.chunk = old_chunk; return s; }
     D.scatter = scatter;
     for (int m = 0; m < 3; ++m) {
-        int occ = substep_occupancy(m, D.scatter, D.chunk);
+        int occ = substep_occupancy(m, D.scatter, D.chunk, D.xm != 0);
         ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->use_graph = use_graph != 0;

@@ -29,11 +29,12 @@ __global__ void k_bgdo_accum(Dev D, const float4 *__restrict__ key, const float4
         const float mu = r6.z, lam = r6.w;
         const int elastic = __float_as_int(r7.y) & 15;
         Sym t;
-        if (elastic == 0) {
-            float U[9], V[9], s[3], e[3], d[3];
+        float U[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}, s[3] = {1.f, 1.f, 1.f}, e[3] = {0.f, 0.f, 0.f};
+        if (elastic_needs_svd(elastic)) {
+            float V[9], d[3];
             if (svd3_robust(F, U, V, s, e, d) == 2) set_err(D, ERRB_NONFINITE);
-            t = tau_fcr(U, s, e, mu, lam);
-        } else if (!tau_nh(F, mu, lam, t)) {
+        }
+        if (!kirchhoff(elastic, F, U, s, e, mu, lam, t)) {
             set_err(D, ERRB_NONFINITE);
             t = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         }

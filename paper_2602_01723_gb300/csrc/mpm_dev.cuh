@@ -65,6 +65,7 @@ struct Dev {
     unsigned max_chunks;
     int chunk;             // particles per chunk
     int scatter;           // scatter strategy of the substep kernel (0 shared tile, 2 direct)
+    int xm;                // the material table uses models beyond FCR / NH / VM / DP
     unsigned *err;         // sticky error bits
 };
 

@@ -337,7 +337,11 @@ template <int TPB> struct SubstepSmem {
 // TPB: threads per CTA = largest chunk (one particle per thread); 64 or 128.
 // Both variants cap registers at 128 (16 warps per SM); the 64-thread one
 // runs twice as many independent CTAs, which overlap each other's staging.
-template <int MODE, int SCAT, int TPB>
+// XM: the further constitutive models (StVK, Hencky, fluid, volume; fluid and
+// Sigma plasticity).  Without it the kernel handles fixed-corotated and
+// Neo-Hookean with von Mises / Drucker-Prager only, and its register
+// allocation is not shared with the rarer models.
+template <int MODE, int SCAT, int TPB, bool XM>
 __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int spar) {
     extern __shared__ float4 smem_raw[];
     SubstepSmem<TPB> &S = *reinterpret_cast<SubstepSmem<TPB> *>(smem_raw);
@@ -491,8 +495,15 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                     for (int cc = 0; cc < 3; ++cc)
                         G[3 * rr + cc] = F[3 * rr + cc] + dt * (Cm[3 * rr] * F[cc] + Cm[3 * rr + 1] * F[3 + cc] +
                                                                 Cm[3 * rr + 2] * F[6 + cc]);
-                // one SVD of the updated F serves the return map and the next stress
-                if (plastic != PLASTIC_NONE || (SCATTER && elastic == 0)) {
+                if (XM && plastic >= PLASTIC_FLUID) {
+                    // volume-only plasticity: F = c I, whose SVD is U = V = I, s = c
+                    const float cm1 = volume_plastic(plastic, G);
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) U[t] = (t % 4 == 0) ? 1.f : 0.f;
+#pragma unroll
+                    for (int t = 0; t < 3; ++t) { s3[t] = 1.f + cm1; e3[t] = cm1; }
+                } else if (plastic != PLASTIC_NONE || (SCATTER && (XM ? elastic_needs_svd(elastic) : elastic == 0))) {
+                    // one SVD of the updated F serves the return map and the next stress
                     float Vv[9], d3[3];
                     const int fb = svd3_robust(G, U, Vv, s3, e3, d3);
                     if (fb) {
@@ -521,7 +532,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 const float4 r2 = nr[2], r3 = nr[3];
                 Cm[0] = r2.x; Cm[1] = r2.y; Cm[2] = r2.z; Cm[3] = r2.w;
                 Cm[4] = r3.x; Cm[5] = r3.y; Cm[6] = r3.z; Cm[7] = r3.w;
-                if (elastic == 0) {
+                if (XM ? elastic_needs_svd(elastic) : elastic == 0) {
                     float Vv[9], d3[3];
                     const int fb = svd3_robust(F, U, Vv, s3, e3, d3);
                     if (fb) {
@@ -538,9 +549,11 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 // Kirchhoff stress of F (App. B.1 / App. A) and the affine momentum
                 // A = m C - 4 dt V / dx^2 tau of the §4.2 equation, as Ad = A dx
                 Sym tau;
-                if (elastic == 0) {
-                    tau = tau_fcr(U, s3, e3, mu, lam);
-                } else if (!tau_nh(F, mu, lam, tau)) {
+                bool tau_ok = true;
+                if (XM) tau_ok = kirchhoff(elastic, F, U, s3, e3, mu, lam, tau);
+                else if (elastic == ELASTIC_FCR) tau = tau_fcr(U, s3, e3, mu, lam);
+                else tau_ok = tau_nh(F, mu, lam, tau);
+                if (!tau_ok) {
                     set_err(D, ERRB_NONFINITE);
                     tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
                 }
@@ -787,20 +800,27 @@ void launch_plan(const Dev &D, int bump_mask, cudaStream_t st) { k_plan<<<1, 102
 void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st) {
     k_prepare<<<grid, 256, 0, st>>>(D, upd_par, act_par, do_sort, keep_momentum);
 }
-template <int MODE, int SCAT, int TPB> static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
-    k_substep<MODE, SCAT, TPB><<<grid, TPB, sizeof(SubstepSmem<TPB>), st>>>(D, gpar, spar);
+template <int MODE, int SCAT, int TPB, bool XM>
+static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
+    k_substep<MODE, SCAT, TPB, XM><<<grid, TPB, sizeof(SubstepSmem<TPB>), st>>>(D, gpar, spar);
 }
 template <int TPB> static void launch_tpb(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st) {
-    if (mode == MODE_G2P) { launch_sub<MODE_G2P, 2, TPB>(D, gpar, spar, grid, st); return; }
-    if (mode == MODE_P2G) {
-        if (D.scatter == 0) launch_sub<MODE_P2G, 0, TPB>(D, gpar, spar, grid, st);
-        else if (D.scatter == 1) launch_sub<MODE_P2G, 1, TPB>(D, gpar, spar, grid, st);
-        else launch_sub<MODE_P2G, 2, TPB>(D, gpar, spar, grid, st);
+    if (D.xm) {   // further models: the shared-memory fixed-point scatter only
+        if (mode == MODE_G2P) launch_sub<MODE_G2P, 2, TPB, true>(D, gpar, spar, grid, st);
+        else if (mode == MODE_P2G) launch_sub<MODE_P2G, 1, TPB, true>(D, gpar, spar, grid, st);
+        else launch_sub<MODE_FUSED, 1, TPB, true>(D, gpar, spar, grid, st);
         return;
     }
-    if (D.scatter == 0) launch_sub<MODE_FUSED, 0, TPB>(D, gpar, spar, grid, st);
-    else if (D.scatter == 1) launch_sub<MODE_FUSED, 1, TPB>(D, gpar, spar, grid, st);
-    else launch_sub<MODE_FUSED, 2, TPB>(D, gpar, spar, grid, st);
+    if (mode == MODE_G2P) { launch_sub<MODE_G2P, 2, TPB, false>(D, gpar, spar, grid, st); return; }
+    if (mode == MODE_P2G) {
+        if (D.scatter == 0) launch_sub<MODE_P2G, 0, TPB, false>(D, gpar, spar, grid, st);
+        else if (D.scatter == 1) launch_sub<MODE_P2G, 1, TPB, false>(D, gpar, spar, grid, st);
+        else launch_sub<MODE_P2G, 2, TPB, false>(D, gpar, spar, grid, st);
+        return;
+    }
+    if (D.scatter == 0) launch_sub<MODE_FUSED, 0, TPB, false>(D, gpar, spar, grid, st);
+    else if (D.scatter == 1) launch_sub<MODE_FUSED, 1, TPB, false>(D, gpar, spar, grid, st);
+    else launch_sub<MODE_FUSED, 2, TPB, false>(D, gpar, spar, grid, st);
 }
 // the chunk size selects the CTA size: chunks of <= 64 particles run 64-thread CTAs
 void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st) {
@@ -814,22 +834,27 @@ void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStr
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st) {
     k_grid_dense<<<1024, 256, 0, st>>>(D, par, which, m, mv);
 }
-template <int MODE, int SCAT, int TPB> static int occ_of() {
+template <int MODE, int SCAT, int TPB, bool XM> static int occ_of() {
     int nb = 0;
-    cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SubstepSmem<TPB>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT, TPB>, TPB, sizeof(SubstepSmem<TPB>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT, TPB, XM>, TPB, sizeof(SubstepSmem<TPB>));
     return nb;
 }
-template <int TPB> static int occ_tpb(int mode, int scatter) {
-    if (mode == MODE_G2P) return occ_of<MODE_G2P, 2, TPB>();
+template <int TPB> static int occ_tpb(int mode, int scatter, bool xm) {
+    if (xm)
+        return mode == MODE_G2P ? occ_of<MODE_G2P, 2, TPB, true>()
+                                : mode == MODE_P2G ? occ_of<MODE_P2G, 1, TPB, true>() : occ_of<MODE_FUSED, 1, TPB, true>();
+    if (mode == MODE_G2P) return occ_of<MODE_G2P, 2, TPB, false>();
     if (mode == MODE_P2G)
-        return scatter == 0 ? occ_of<MODE_P2G, 0, TPB>() : scatter == 1 ? occ_of<MODE_P2G, 1, TPB>() : occ_of<MODE_P2G, 2, TPB>();
-    return scatter == 0 ? occ_of<MODE_FUSED, 0, TPB>() : scatter == 1 ? occ_of<MODE_FUSED, 1, TPB>() : occ_of<MODE_FUSED, 2, TPB>();
+        return scatter == 0 ? occ_of<MODE_P2G, 0, TPB, false>()
+                            : scatter == 1 ? occ_of<MODE_P2G, 1, TPB, false>() : occ_of<MODE_P2G, 2, TPB, false>();
+    return scatter == 0 ? occ_of<MODE_FUSED, 0, TPB, false>()
+                        : scatter == 1 ? occ_of<MODE_FUSED, 1, TPB, false>() : occ_of<MODE_FUSED, 2, TPB, false>();
 }
-// resident CTAs per SM of the substep kernel for a mode, scatter strategy and chunk size
-int substep_occupancy(int mode, int scatter, int chunk) {
-    return chunk <= 64 ? occ_tpb<64>(mode, scatter) : occ_tpb<128>(mode, scatter);
+// resident CTAs per SM of the substep kernel for a mode, scatter strategy, chunk size and model set
+int substep_occupancy(int mode, int scatter, int chunk, bool xm) {
+    return chunk <= 64 ? occ_tpb<64>(mode, scatter, xm) : occ_tpb<128>(mode, scatter, xm);
 }
 int substep_chunk_max() { return CH_MAX; }
 

@@ -38,7 +38,7 @@ void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int kee
 void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st);
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st);
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
-int substep_occupancy(int mode, int scatter, int chunk);
+int substep_occupancy(int mode, int scatter, int chunk, bool xm);
 int substep_chunk_max();
 
 // recorded trajectory and reverse-pass buffers

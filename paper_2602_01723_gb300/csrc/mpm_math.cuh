@@ -330,6 +330,105 @@ __device__ __forceinline__ bool tau_nh(const float F[9], float mu, float lam, Sy
 }
 
 // ---------------------------------------------------------------------------
+// Further elastic models of App. B.1 (kept out of line: the substep kernel's
+// register allocation stays that of the fixed-corotated / Neo-Hookean path)
+//   2 StVK, Green strain E = (F^T F - I)/2:
+//       tau = 2 mu F E F^T + lambda J (J - 1) I
+//   3 Hencky (SigmaElasticity; also App. A's StVK, whose P F^T is this):
+//       tau = U diag(2 mu eps + lambda tr eps) U^T, eps = log max(s, 1e-4)
+//   4 fluid:  tau = lambda J (J - 1) I
+//   5 volume: tau = kappa (J - 1/J) I, kappa = 2 mu / 3 + lambda (gamma = 2)
+// Returns false when the state is outside the model's domain (J <= 0 for 5).
+// ---------------------------------------------------------------------------
+enum { ELASTIC_FCR = 0, ELASTIC_NH = 1, ELASTIC_STVK = 2, ELASTIC_HENCKY = 3, ELASTIC_FLUID = 4,
+       ELASTIC_VOLUME = 5 };
+#define MPM_SIGMA_FLOOR 1e-4f
+
+__device__ __forceinline__ bool elastic_needs_svd(int elastic) {
+    return elastic == ELASTIC_FCR || elastic == ELASTIC_HENCKY;
+}
+
+static __device__ __noinline__ bool tau_more(int elastic, const float *F, const float *U, const float *s, const float *e,
+                                      float mu, float lam, Sym *out) {
+    Sym t{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const float jm1 = det_minus_one(F);
+    bool ok = true;
+    if (elastic == ELASTIC_STVK) {
+        float h[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) h[i] = F[i];
+        h[0] -= 1.f; h[4] -= 1.f; h[8] -= 1.f;
+        float E[9];   // (H + H^T + H^T H) / 2
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                E[3 * i + j] = 0.5f * (h[3 * i + j] + h[3 * j + i] + h[i] * h[j] + h[3 + i] * h[3 + j] +
+                                       h[6 + i] * h[6 + j]);
+        float A[9];   // F E
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                A[3 * i + j] = F[3 * i] * E[j] + F[3 * i + 1] * E[3 + j] + F[3 * i + 2] * E[6 + j];
+        const float k = 2.f * mu, vol = lam * (1.f + jm1) * jm1;
+        t.xx = k * (A[0] * F[0] + A[1] * F[1] + A[2] * F[2]) + vol;
+        t.yy = k * (A[3] * F[3] + A[4] * F[4] + A[5] * F[5]) + vol;
+        t.zz = k * (A[6] * F[6] + A[7] * F[7] + A[8] * F[8]) + vol;
+        t.xy = k * (A[0] * F[3] + A[1] * F[4] + A[2] * F[5]);
+        t.xz = k * (A[0] * F[6] + A[1] * F[7] + A[2] * F[8]);
+        t.yz = k * (A[3] * F[6] + A[4] * F[7] + A[5] * F[8]);
+    } else if (elastic == ELASTIC_HENCKY) {
+        float eps[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) eps[i] = s[i] > MPM_SIGMA_FLOOR ? log1pf(e[i]) : -9.210340371976184f;
+        const float tr = lam * (eps[0] + eps[1] + eps[2]);
+        const float d0 = 2.f * mu * eps[0] + tr, d1 = 2.f * mu * eps[1] + tr, d2 = 2.f * mu * eps[2] + tr;
+        t.xx = d0 * U[0] * U[0] + d1 * U[1] * U[1] + d2 * U[2] * U[2];
+        t.yy = d0 * U[3] * U[3] + d1 * U[4] * U[4] + d2 * U[5] * U[5];
+        t.zz = d0 * U[6] * U[6] + d1 * U[7] * U[7] + d2 * U[8] * U[8];
+        t.xy = d0 * U[0] * U[3] + d1 * U[1] * U[4] + d2 * U[2] * U[5];
+        t.xz = d0 * U[0] * U[6] + d1 * U[1] * U[7] + d2 * U[2] * U[8];
+        t.yz = d0 * U[3] * U[6] + d1 * U[4] * U[7] + d2 * U[5] * U[8];
+    } else if (elastic == ELASTIC_FLUID) {
+        t.xx = t.yy = t.zz = lam * (1.f + jm1) * jm1;
+    } else if (elastic == ELASTIC_VOLUME) {
+        if (jm1 > -1.f) {
+            // J - 1/J = (J - 1)(J + 1) / J
+            t.xx = t.yy = t.zz = (2.f * mu / 3.f + lam) * jm1 * (2.f + jm1) / (1.f + jm1);
+        } else {
+            ok = false;
+        }
+    } else {
+        ok = false;
+    }
+    *out = t;
+    return ok;
+}
+
+// Kirchhoff stress of any elastic model; U, s, e must hold the SVD of F when
+// elastic_needs_svd(elastic)
+__device__ __forceinline__ bool kirchhoff(int elastic, const float F[9], const float U[9], const float s[3],
+                                          const float e[3], float mu, float lam, Sym &t) {
+    if (elastic == ELASTIC_FCR) { t = tau_fcr(U, s, e, mu, lam); return true; }
+    if (elastic == ELASTIC_NH) return tau_nh(F, mu, lam, t);
+    return tau_more(elastic, F, U, s, e, mu, lam, &t);
+}
+
+// Volume-only plasticity: 3 fluid (App. A): F <- J^{1/3} I; 4 Sigma
+// (App. B.2): J clamped to [0.05, 1.2], F <- J^{1/3} I.  Writes c I into G
+// and returns c - 1 (cbrt keeps the sign of an inverted J under 3).
+static __device__ __noinline__ float volume_plastic(int plastic, float *G) {
+    float jm1 = det_minus_one(G);
+    if (plastic == 4) jm1 = fminf(fmaxf(jm1, 0.05f - 1.f), 1.2f - 1.f);
+    const float cm1 = jm1 > -1.f ? expm1f(log1pf(jm1) * (1.f / 3.f)) : cbrtf(1.f + jm1) - 1.f;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) G[i] = 0.f;
+    G[0] = G[4] = G[8] = 1.f + cm1;
+    return cm1;
+}
+
+// ---------------------------------------------------------------------------
 // Return maps on the singular values (von Mises, Drucker-Prager with zero
 // cohesion).  eps = log(max(s, 1e-4)); eps_hat its deviatoric part.
 //   VM: dgamma = |eps_hat| - yield/(2 mu)
@@ -339,9 +438,8 @@ __device__ __forceinline__ bool tau_nh(const float F[9], float mu, float lam, Sy
 // On return z = new singular values and ze = z - 1.  Returns 0 elastic,
 // 1 projected, 2 cone tip.
 // ---------------------------------------------------------------------------
-enum { PLASTIC_NONE = 0, PLASTIC_VM = 1, PLASTIC_DP = 2 };
+enum { PLASTIC_NONE = 0, PLASTIC_VM = 1, PLASTIC_DP = 2, PLASTIC_FLUID = 3, PLASTIC_SIGMA = 4 };
 enum { RM_ELASTIC = 0, RM_PROJECT = 1, RM_TIP = 2 };
-#define MPM_SIGMA_FLOOR 1e-4f
 
 __device__ __forceinline__ float log_sigma(float s, float d) {
     // log(s) = 0.5 log1p(s^2 - 1) keeps precision near s = 1

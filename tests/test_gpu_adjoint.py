@@ -1,5 +1,7 @@
 """GPU reverse pass (hand-written adjoint with checkpoint recompute) against
-the FP64 oracle's adjoint and against FP64 central finite differences.
+the FP64 oracle's adjoint and against FP64 central finite differences.  Each
+side runs its own forward from the same seeded inputs and forms its own loss
+gradient; nothing the CUDA path computes is fed to the oracle.
 
 Tolerance: gradients within 1e-3 relative, ||g_gpu - g_ref||_2 / ||g_ref||_2
 per parameter kind."""
@@ -40,7 +42,6 @@ def one_substep_case(orc, sim_mod, sc, v, C, F, params=None, seed=0):
     cx = rng.standard_normal((sc.n, 3)).astype(np.float32)
     s = sim_mod.Simulator.from_scene(sc, ckpt_every=20)
     s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F, params=params)
-    st0 = {k: t.double().cpu().numpy() for k, t in s.get().items()}
     s.step(1, record=True)
     g, a0 = s.backward([1], torch.as_tensor(cx[None]), want_state0=True)
     g = g.double().cpu().numpy()
@@ -50,7 +51,7 @@ def one_substep_case(orc, sim_mod, sc, v, C, F, params=None, seed=0):
     mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, params)
     adj_out = np.zeros((sc.n, 24))
     adj_out[:, 0:3] = cx
-    ai, gr = orc.substep_adjoint(cfg, orc.new_state(st0["x"], st0["v"], st0["C"], st0["F"]), mat, adj_out)
+    ai, gr = orc.substep_adjoint(cfg, orc.new_state(sc.x, v, C, F), mat, adj_out)
     return g, a0, gr, ai
 
 
@@ -73,41 +74,32 @@ def test_one_substep_adjoint_matches_oracle(orc, sim_mod, kind):
     # return map changes only the stored F; the multi-substep test covers it)
 
 
-def gpu_recorded_run(sim_mod, sc, params, n_sub, frames, target):
-    """GPU forward recorded one substep at a time (so every state is read back
-    for the oracle), then the reverse pass for the frame MSE loss.  Returns
-    the GPU gradient, the GPU states (n_sub+1, n, 24) and dL/dx."""
+def frame_loss_gradients(orc, sim_mod, sc, params, n_sub, frames, target):
+    """The frame MSE loss L = 1/(F N) sum |x_f - target_f|^2 differentiated on
+    both sides: the GPU records its forward, reads the frame positions and
+    runs its reverse pass; the oracle runs its own FP64 forward with a tape
+    and its own adjoint.  Returns (g_gpu, g_oracle), each (n, 3)."""
     s = sim_mod.Simulator.from_scene(sc)
     s.load(sc.x, sc.vol, sc.mat_id, v=sc.v, params=params)
-    tape = np.zeros((n_sub + 1, sc.n, 24))
-
-    def grab(i):
-        st = {k: t.double().cpu().numpy() for k, t in s.get().items()}
-        tape[i] = np.concatenate([st["x"], st["v"], st["C"].reshape(-1, 9), st["F"].reshape(-1, 9)], axis=1)
-
-    grab(0)
-    for i in range(1, n_sub + 1):
-        s.step(1, record=True)
-        grab(i)
-    fx = tape[frames][:, :, 0:3]
+    xs, prev = [], 0
+    for f in frames:
+        s.step(f - prev, record=True)
+        xs.append(s.positions().double().cpu().numpy())
+        prev = f
+    s.step(n_sub - prev, record=True)
     nf = len(frames)
-    dLdx = 2.0 * (fx - target) / (nf * sc.n)
+    dLdx = 2.0 * (np.stack(xs) - target) / (nf * sc.n)
     g = s.backward(frames, torch.as_tensor(dLdx, dtype=torch.float32)).double().cpu().numpy()
     s.close()
-    return g, tape, dLdx
-
-
-def teacher_forced(orc, sim_mod, sc, params, n_sub, frames, target):
-    """GPU gradient vs the FP64 oracle adjoint evaluated on the GPU's own
-    trajectory and loss gradient: isolates the reverse pass's arithmetic."""
-    g, tape, dLdx = gpu_recorded_run(sim_mod, sc, params, n_sub, frames, target)
     cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
     mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, params)
-    _, g_ref = orc.backward(cfg, mat, tape, frames, dLdx)
+    _, tape = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, n_sub, tape=True)
+    _, dLdx_ref = orc.trajectory_loss(tape[frames][:, :, 0:3], target)
+    _, g_ref = orc.backward(cfg, mat, tape, frames, dLdx_ref)
     return g, g_ref
 
 
-def test_multi_substep_adjoint_all_models_teacher_forced(orc, sim_mod):
+def test_multi_substep_adjoint_all_models(orc, sim_mod):
     """30 substeps of a mixed-material ball (FCR, NH, von Mises, Drucker-
     Prager), checkpoint every 20 (two segments), frames at 10, 20, 30; log E,
     nu and yield-stress gradients."""
@@ -122,7 +114,7 @@ def test_multi_substep_adjoint_all_models_teacher_forced(orc, sim_mod):
     sc.v = (sc.v + 2.0 * rng.standard_normal((sc.n, 3))).astype(np.float32)    # shear: plastic flow
     frames = [10, 20, 30]
     target = sc.x[None].astype(np.float64) + 0.01 * rng.standard_normal((3, sc.n, 3))
-    g, g_ref = teacher_forced(orc, sim_mod, sc, params, 30, frames, target)
+    g, g_ref = frame_loss_gradients(orc, sim_mod, sc, params, 30, frames, target)
     for j in range(3):
         assert np.abs(g_ref[:, j]).max() > 0
         assert rel(g[:, j], g_ref[:, j]) < GRAD_TOL, (j, rel(g[:, j], g_ref[:, j]))
@@ -131,10 +123,13 @@ def test_multi_substep_adjoint_all_models_teacher_forced(orc, sim_mod):
 def test_ball_512_trajectory_gradient(orc, sim_mod):
     """The 512-particle, 16^3 copy of the differentiable ball: 400 substeps,
     checkpoint every 20, loss frames every 40 substeps, target from the seeded
-    ground-truth parameters.  (1) the GPU reverse pass against the FP64
-    oracle adjoint on the same trajectory, 1e-3; (2) the oracle's FP64
-    gradient against FP64 central differences of its own loss; (3) the
-    end-to-end GPU gradient (FP32 trajectory) against the FP64 one."""
+    ground-truth parameters.  (1) the oracle's FP64 gradient against FP64
+    central differences of its own loss; (2) the GPU gradient (FP32
+    trajectory and reverse pass) against the FP64 one.  The loss here is
+    ~3e-9: positions nearly match the target, so the FP32 position error of
+    the forward enters dL/dx at the percent level, hence the 10% bound; the
+    1e-3 bound is held where the loss is well conditioned (the tests above
+    and below)."""
     sc = scenes.ball_512()
     frames = [int(f) for f in sc.frame_sub]
     cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
@@ -142,14 +137,8 @@ def test_ball_512_trajectory_gradient(orc, sim_mod):
     mat_true = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.extra["params_true"])
     _, tape_t = orc.run(cfg, st0, mat_true, sc.n_substeps, tape=True)
     target = tape_t[frames][:, :, 0:3]
-    g, g_tf = teacher_forced(orc, sim_mod, sc, sc.params, sc.n_substeps, frames, target)
-    assert rel(g[:, 0], g_tf[:, 0]) < GRAD_TOL
-    assert rel(g[:, 1], g_tf[:, 1]) < GRAD_TOL
-    # FP64 trajectory gradient and central differences
+    g, g64 = frame_loss_gradients(orc, sim_mod, sc, sc.params, sc.n_substeps, frames, target)
     mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params)
-    _, tape = orc.run(cfg, st0, mat, sc.n_substeps, tape=True)
-    L, dLdx = orc.trajectory_loss(tape[frames][:, :, 0:3], target)
-    _, g64 = orc.backward(cfg, mat, tape, frames, dLdx)
     for p in np.argsort(-np.abs(g64[:, 0]))[:2]:
         h = 1e-3
         fl = []
@@ -160,19 +149,18 @@ def test_ball_512_trajectory_gradient(orc, sim_mod):
             fl.append(orc.trajectory_loss(tp[frames][:, :, 0:3], target)[0])
         fd = (fl[0] - fl[1]) / (2 * h)
         assert abs(g64[p, 0] - fd) < 1e-3 * abs(fd), (p, g64[p, 0], fd)
-    # end to end: the FP32 trajectory's gradient against the FP64 one; the
-    # loss here is ~3e-9, so the FP32 position error enters at the percent level
     assert rel(g[:, 0], g64[:, 0]) < 0.1
 
 
-def test_ball_50k_full_size_gradient_teacher_forced(orc, sim_mod):
+def test_ball_50k_full_size_gradient(orc, sim_mod):
     """The 50k-particle, 64^3 ball at full size: 100 substeps (5 checkpoint
-    segments) covering the first floor contact, frames at 60 and 100."""
+    segments) covering the first floor contact, frames at 60 and 100, a target
+    offset from the start (a well-conditioned loss)."""
     sc = scenes.ball_50k()
     frames = [60, 100]
     rng = np.random.default_rng(7)
     target = sc.x[None].astype(np.float64) + np.array([0.0, -0.01, 0.0]) + 0.002 * rng.standard_normal((2, sc.n, 3))
-    g, g_ref = teacher_forced(orc, sim_mod, sc, sc.params, 100, frames, target)
+    g, g_ref = frame_loss_gradients(orc, sim_mod, sc, sc.params, 100, frames, target)
     assert np.abs(g_ref[:, 0]).max() > 0
     assert rel(g[:, 0], g_ref[:, 0]) < GRAD_TOL
     assert rel(g[:, 1], g_ref[:, 1]) < GRAD_TOL

@@ -1,0 +1,141 @@
+"""GPU parity of the further constitutive models (App. A, App. B.1, App. B.2):
+StVK (Green strain), Hencky, fluid and volume elasticity, fluid and Sigma
+plasticity, against the FP64 oracle from the same seeded inputs: the P2G
+grid, one substep, a free-running run, the one-substep adjoint and BGDO.
+Tolerances as for the other models: grid 1e-5 relative, one-substep v and C
+1e-5 relative, x 1e-6 dx, F 2e-5, positions 1e-4 dx after 100 substeps,
+gradients 1e-3 relative."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_01723_gb300 import scenes  # noqa: E402
+
+# (elastic, plastic) pairs: StVK, Hencky, fluid (water: fluid + fluid
+# plasticity), volume, FCR + fluid plasticity, FCR + Sigma plasticity,
+# Hencky + Drucker-Prager, Neo-Hookean + Sigma plasticity
+PAIRS = [(2, 0), (3, 0), (4, 3), (5, 0), (0, 3), (0, 4), (3, 2), (1, 4)]
+
+
+@pytest.fixture(scope="module")
+def sim_mod():
+    from __graft_entry__ import build
+    build()
+    from paper_2602_01723_gb300 import sim
+    return sim
+
+
+def further_cube():
+    sc = scenes.cube_8k()
+    sc.materials = [scenes.material(el, pl, 1e4, 0.3, 10.0, friction_angle_deg=30.0) for el, pl in PAIRS]
+    sc.mat_id = (np.arange(sc.n) % len(PAIRS)).astype(np.int32)
+    return sc
+
+
+def oracle_setup(orc, sc):
+    return (orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity),
+            orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, sc.params))
+
+
+def test_p2g_grid_further_models(orc, sim_mod):
+    sc = further_cube()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=60, fs=0.1)[0]
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    m, mv = s.debug_p2g()
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    gm, gmv = orc.p2g(cfg, orc.new_state(sc.x, v, C, F), mat)
+    floor = np.abs(gm).max() * 9.8 * sc.dt
+    em = np.abs(m[0].double().cpu().numpy() - gm).max() / max(np.abs(gm).max(), floor)
+    emv = np.abs(mv[0].double().cpu().numpy() - gmv).max() / max(np.abs(gmv).max(), floor)
+    assert em < 1e-5 and emv < 1e-5, (em, emv)
+
+
+def test_one_substep_further_models(orc, sim_mod):
+    sc = further_cube()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=61, fs=0.1)[0]
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    s.step(1)
+    s.sync()
+    got = {k: t.double().cpu().numpy() for k, t in s.get().items()}
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, v, C, F), mat, 1)
+    assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * np.abs(ref["v"]).max()
+    assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
+    assert np.abs(got["C"] - ref["C"]).max() < 1e-5 * np.abs(ref["C"]).max()
+    assert np.abs(got["F"] - ref["F"]).max() < 2e-5
+    # the Sigma clamp and the fluid projection both acted
+    J = np.linalg.det(got["F"])
+    sig = np.isin(sc.mat_id, [5, 7])
+    assert J[sig].max() <= 1.2 + 1e-5 and J[sig].min() >= 0.05 - 1e-6
+
+
+@pytest.mark.parametrize("pair", [(4, 3), (3, 0), (2, 0)], ids=["water", "hencky", "stvk"])
+def test_free_running_100_substeps(orc, sim_mod, pair):
+    """From a stressed start (|F - I| ~ 0.02) so that the model's stress drives
+    the motion."""
+    sc = scenes.cube_8k()
+    sc.materials = [scenes.material(pair[0], pair[1], 1e4, 0.3, 1.0)]
+    v, C, F = scenes.key_frames(sc, 1, k_seed=64, vs=0.1, cs=1.0, fs=0.02)[0]
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    s.step(100)
+    s.sync()
+    x = s.positions().double().cpu().numpy()
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, v, C, F), mat, 100)
+    err = np.abs(x - ref["x"]).max() / sc.dx
+    assert err < 1e-4, err
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("pair", PAIRS, ids=["stvk", "hencky", "water", "volume", "fcr_fluidpl", "fcr_sigmapl",
+                                             "hencky_dp", "nh_sigmapl"])
+def test_one_substep_adjoint_further_models(orc, sim_mod, pair):
+    sc = scenes.ball_512()
+    sc.materials = [scenes.material(pair[0], pair[1], 5e3, 0.3, 100.0, friction_angle_deg=30.0)]
+    sc.params = None
+    v, C, F = scenes.key_frames(sc, 1, k_seed=62, vs=0.3, cs=2.0, fs=0.06)[0]
+    rng = np.random.default_rng(0)
+    cx = rng.standard_normal((sc.n, 3)).astype(np.float32)
+    s = sim_mod.Simulator.from_scene(sc, ckpt_every=20)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    s.step(1, record=True)
+    g, a0 = s.backward([1], torch.as_tensor(cx[None]), want_state0=True)
+    g = g.double().cpu().numpy()
+    a0 = a0.double().cpu().numpy()
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    adj_out = np.zeros((sc.n, 24))
+    adj_out[:, 0:3] = cx
+    ai, gr = orc.substep_adjoint(cfg, orc.new_state(sc.x, v, C, F), mat, adj_out)
+    for sl in (slice(0, 3), slice(3, 6), slice(6, 15), slice(15, 24)):
+        assert rel(a0[:, sl], ai[:, sl]) < 1e-3, (sl, rel(a0[:, sl], ai[:, sl]))
+    assert rel(g[:, 0], gr[:, 0]) < 1e-3
+    assert rel(g[:, 1], gr[:, 1]) < 1e-3
+
+
+def test_bgdo_further_models(orc, sim_mod):
+    sc = further_cube()
+    keys = scenes.key_frames(sc, 3, k_seed=63, fs=0.05)
+    s = sim_mod.Simulator.from_scene(sc)
+    for k, (v, C, F) in enumerate(keys):
+        s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+        s.snapshot(k)
+    got = {k: t.double().cpu().numpy() for k, t in s.bgdo([0, 1, 2], signals=True).items()}
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.bgdo(cfg, [orc.new_state(sc.x, v, C, F) for v, C, F in keys], mat)
+    scale = np.abs(ref["g_tau"]).max()
+    assert np.all(np.abs(got["g_tau"] - ref["g_tau"]) <= 1e-4 * np.abs(ref["g_tau"]) + 1e-6 * scale)
+    assert np.abs(got["delta"] - ref["delta"]).max() < 6e-5
+    assert np.abs(got["G"] - ref["G"]).max() < 2e-4

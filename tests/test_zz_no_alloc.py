@@ -107,7 +107,14 @@ def test_noalloc_matches_context_path_on_two_calls_in_a_row():
     _close(n1, _context_step(sc, s0), _oracle_step(sc, s0), sc)
     st, n2 = _noalloc(sc, n1)          # second call: the scratch holds the first call's grid
     assert st == 0
-    _close(n2, _context_step(sc, n1), _oracle_step(sc, n1), sc)
+    # against the oracle's own two substeps from the seeded state (two
+    # substeps' error: within twice the one-substep bound), and against the
+    # context path applied to the same input
+    ref2 = _oracle_step(sc, _oracle_step(sc, s0))
+    e_ref = _errors(n2, ref2, sc)
+    assert all(e < 2 * t for e, t in zip(e_ref, TOL)), e_ref
+    e_ctx = _errors(n2, _context_step(sc, n1), sc)
+    assert all(e < 2 * t for e, t in zip(e_ctx, TOL)), e_ctx
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch():
