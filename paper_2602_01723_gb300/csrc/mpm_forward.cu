@@ -280,12 +280,17 @@ __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep
 //   MODE_FUSED: G2P(s) + update + return map + stress + P2G(s+1) + binning
 //   MODE_G2P: G2P(s) + update + return map + binning (last substep)
 //
-// One CTA works on one chunk (<= CH particles of one 4^3-node block) at a
-// time:
-//   0. the chunk's records are staged in shared memory by cooperative float4
-//      loads (many requests in flight instead of one dependent chain per
-//      thread), and the grid velocities of the block's 6^3-node gather tile
-//      are loaded;
+// One CTA works on one chunk (<= TPB particles of one 4^3-node block) at a
+// time, one particle per thread, and software-pipelines the chunks it owns
+// (c, c + G, c + 2G, ... for grid size G):
+//   0. staging arrives ahead of use through cp.async copies into shared
+//      memory.  While chunk c is processed, the descriptor of chunk c + 2G,
+//      and the sorted indices and page-table words of chunk c + G are copied
+//      (issued before phase A); the records of chunk c + G (warp-coalesced:
+//      each copy instruction moves four whole 128-byte records) and the grid
+//      velocities of its 6^3-node gather tile (issued after phase A, when
+//      those buffers are free) arrive during phases B and flush.  No thread
+//      waits on a dependent global load at the start of a chunk;
 //   A. per particle: gather v and C (App. A G2P), x += dt v, F <- (I + dt C) F,
 //      one SVD serving the return map and the next stress, Kirchhoff stress,
 //      affine momentum A = m C - 4 dt V tau / dx^2 (§4.2); the new record goes
@@ -321,18 +326,96 @@ __device__ __forceinline__ int page_slot(const Dev &D, int par, unsigned ep, int
 __device__ __forceinline__ int node_local(int I, int J, int K) { return ((I & 3) * 4 + (J & 3)) * 4 + (K & 3); }
 
 constexpr int PK_F4 = 5;          // scatter packet: X(3) m | P(3) - | Ad(9) (+3 spare)
+constexpr int RS_F4 = REC_F4 + 1; // staged record stride: 144 B keeps per-thread float4 reads conflict-free
 template <int TPB> struct SubstepSmem {
+    float4 rec[TPB * RS_F4];         // the chunk's records, staged ahead of use
     float4 pk[TPB * PK_F4];          // scatter packets of the chunk's particles
     float4 g[GT3];                   // gather tile: (v, m) per node
     union {
         float f[4 * ST3P];           // scatter tile, component-major [m0 | m1 | m2 | m], padded rows
         int i[4 * ST3P];
     } t;
-    int slot_s[27];                  // pool slot of blocks (B-1 .. B+1)^3 in the scatter grid
-    int slot_g[8];                   // pool slot of blocks (B .. B+1)^3 in the gather grid
+    int4 cd[3];                      // chunk descriptors, ring of (c, c + G, c + 2G)
+    unsigned pidx[TPB];              // sorted particle indices of the next chunk
+    unsigned pe[35];                 // page-table words of the next chunk: epoch ...
+    int ps[35];                      // ... and pool slot; 0..26 scatter blocks, 27..34 gather blocks
+    int slot_s[2][27];               // pool slot of blocks (B-1 .. B+1)^3 in the scatter grid, per chunk parity
     float red[2 * (TPB / 32)];
     float scale[2];
 };
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ---- staging steps (every thread of the CTA calls them) ---------------------
+// level 2: sorted indices of chunk ch and its page-table lookups: 27
+// scatter-grid blocks (B-1 .. B+1)^3 and 8 gather-grid blocks (B .. B+1)^3,
+// one per thread of the last two warps; a block outside the grid gets an
+// epoch that never matches
+template <int TPB, bool GATHER, bool SCATTER>
+__device__ __forceinline__ void stage_level2(const Dev &D, SubstepSmem<TPB> &S, int4 ch, int gpar, int spar,
+                                             unsigned ep_g, unsigned ep_s) {
+    const int tid = threadIdx.x;
+    if (tid < ch.z) cp_async4(&S.pidx[tid], D.sorted + ch.y + tid);
+    int inst, bx, by, bz;
+    key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+    const int t = tid - (TPB - 64 > 0 ? 64 : 0);    // the lookups go to the last warps of the CTA
+    if (t >= 0 && t < 35 && (t < 27 ? SCATTER : GATHER)) {
+        int qx, qy, qz, par;
+        unsigned ep;
+        if (t < 27) { qx = bx + t / 9 - 1; qy = by + (t / 3) % 3 - 1; qz = bz + t % 3 - 1; par = spar; ep = ep_s; }
+        else { const int u = t - 27; qx = bx + (u >> 2); qy = by + ((u >> 1) & 1); qz = bz + (u & 1); par = gpar; ep = ep_g; }
+        if (qx < 0 || qy < 0 || qz < 0 || qx >= D.NB[0] || qy >= D.NB[1] || qz >= D.NB[2]) {
+            S.pe[t] = ep + 1u;
+            S.ps[t] = -1;
+        } else {
+            const unsigned k = block_key(D, inst, qx, qy, qz);
+            cp_async4(&S.pe[t], D.page_epoch[par] + k);
+            cp_async4(&S.ps[t], D.page[par] + k);
+        }
+    }
+}
+
+// level 3: the chunk's records (warp-coalesced: instruction w of a warp moves
+// float4 l % 8 of records 4 w + l / 8 of the warp's 32) and its gather tile.
+// Needs the level-2 words of the chunk in shared memory.
+template <int TPB, bool GATHER>
+__device__ __forceinline__ void stage_level3(const Dev &D, SubstepSmem<TPB> &S, int4 ch, int gpar, unsigned ep_g) {
+    const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31;
+    const int piece = lane & 7;
+    if (!GATHER || (piece != 2 && piece != 3)) {   // G2P does not read the old C
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int j = wbase + 4 * w + (lane >> 3);
+            if (j < ch.z) cp_async16(&S.rec[j * RS_F4 + piece], D.rec + (size_t)S.pidx[j] * REC_F4 + piece);
+        }
+    }
+    if (GATHER) {
+        int inst, bx, by, bz;
+        key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+        for (int t = tid; t < GT3; t += TPB) {
+            const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+            const int b = 27 + (((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2));
+            const int sl = S.pe[b] == ep_g ? S.ps[b] : -1;
+            if (sl >= 0) cp_async16(&S.g[t], D.gv[gpar] + (size_t)sl * BLK_NODES + node_local(i, j, k));
+            else S.g[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+}
+
+// pool slots of the scatter blocks from the level-2 words (threads 27 of the last warps)
+template <int TPB>
+__device__ __forceinline__ void stage_slots(SubstepSmem<TPB> &S, int buf, unsigned ep_s) {
+    const int t = threadIdx.x - (TPB - 64 > 0 ? 64 : 0);
+    if (t >= 0 && t < 27) S.slot_s[buf][t] = S.pe[t] == ep_s ? S.ps[t] : -1;
+}
 
 // TPB: threads per CTA = largest chunk (one particle per thread); 64 or 128.
 // Both variants cap registers at 128 (16 warps per SM); the 64-thread one
@@ -351,69 +434,52 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
     const unsigned ep_g = GATHER ? D.ctr[CTR_EPOCH_OF + gpar] : 0u;
     const unsigned ep_s = SCATTER ? D.ctr[CTR_EPOCH_OF + spar] : 0u;
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
-    const int tid = threadIdx.x, T = blockDim.x;
+    const int tid = threadIdx.x, T = TPB;
+    unsigned c = blockIdx.x;
+    if (c >= n_chunks) return;
 
-    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-        const int4 ch = D.chunks[c];
+    // prologue: descriptors of chunks c and c + G; levels 2 and 3 of chunk c
+    if (tid == 0) {
+        S.cd[0] = D.chunks[c];
+        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+    }
+    if (SCATTER && SCAT != 2)
+        for (int t = tid; t < 4 * ST3P; t += T) S.t.i[t] = 0;
+    __syncthreads();
+    stage_level2<TPB, GATHER, SCATTER>(D, S, S.cd[0], gpar, spar, ep_g, ep_s);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+    if (SCATTER) stage_slots<TPB>(S, 0, ep_s);
+    stage_level3<TPB, GATHER>(D, S, S.cd[0], gpar, ep_g);
+    cp_async_commit();
+    cp_async_wait_all();
+    __syncthreads();
+
+    for (int kc = 0;; ++kc) {
+        const int4 ch = S.cd[kc % 3];
         const int cnt = min(ch.z, TPB);
+        const unsigned cn = c + gridDim.x;
+        const bool has_next = cn < n_chunks;
+        const unsigned p_cur = tid < cnt ? S.pidx[tid] : 0u;   // read before level 2 of c + G overwrites it
+        // level 1 of chunk c + 2G and level 2 of chunk c + G, in flight during phase A
+        if (tid == 0 && cn + gridDim.x < n_chunks) cp_async16(&S.cd[(kc + 2) % 3], D.chunks + cn + gridDim.x);
+        if (has_next) stage_level2<TPB, GATHER, SCATTER>(D, S, S.cd[(kc + 1) % 3], gpar, spar, ep_g, ep_s);
+        cp_async_commit();
         int inst, bx, by, bz;
         key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
         const int ox = bx * BLK, oy = by * BLK, oz = bz * BLK;   // gather tile origin (node)
-
-        // ---- 0. staging: two round trips --------------------------------------
-        // (1) the sorted index of this thread's first particle and the pool
-        //     slots of the tiles' blocks; (2) the particle's record, straight
-        //     into registers (all float4 loads issued together), and the
-        //     gather tile.
-        const int rounds = (cnt + T - 1) / T;
-        unsigned p_next = tid < cnt ? D.sorted[ch.y + tid] : 0u;
-        if (SCATTER && tid < 27)
-            S.slot_s[tid] = page_slot(D, spar, ep_s, inst, bx + tid / 9 - 1, by + (tid / 3) % 3 - 1, bz + tid % 3 - 1);
-        if (GATHER && tid < 8)
-            S.slot_g[tid] = page_slot(D, gpar, ep_g, inst, bx + (tid >> 2), by + ((tid >> 1) & 1), bz + (tid & 1));
-        if (SCATTER && SCAT != 2)
-            for (int t = tid; t < 4 * ST3P; t += T) S.t.i[t] = 0;
-        __syncthreads();
-        float4 nr[REC_F4];
-        if (tid < cnt) {
-            const float4 *src = D.rec + (size_t)p_next * REC_F4;
-#pragma unroll
-            for (int w = 0; w < REC_F4; ++w)
-                if (!GATHER || (w != 2 && w != 3)) nr[w] = src[w];   // G2P does not read the old C
-        }
-        if (GATHER) {
-            constexpr int GU = (GT3 + TPB - 1) / TPB;   // tile nodes per thread
-            float4 gt[GU];
-#pragma unroll
-            for (int u = 0; u < GU; ++u) {
-                const int t = tid + u * TPB;
-                gt[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (t < GT3) {
-                    const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
-                    const int sl = S.slot_g[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
-                    if (sl >= 0) gt[u] = D.gv[gpar][(size_t)sl * BLK_NODES + node_local(i, j, k)];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < GU; ++u)
-                if (tid + u * TPB < GT3) S.g[tid + u * TPB] = gt[u];
-        }
-        __syncthreads();
+        const int rounds = 1;
 
         // ---- A. per-particle update -----------------------------------------
         float bnd_m = 0.f, bnd_v = 0.f;
-        for (int r = 0; r < rounds; ++r) {
-            const int j = r * T + tid;
+        {
+            const int j = tid;
             const bool valid = j < cnt;
             const unsigned lane_mask = __ballot_sync(0xffffffffu, valid);
-            if (!valid) continue;
-            const unsigned p = r == 0 ? p_next : D.sorted[ch.y + j];
-            if (r > 0) {   // later rounds (chunks larger than the CTA) load here
-                const float4 *src = D.rec + (size_t)p * REC_F4;
-#pragma unroll
-                for (int w = 0; w < REC_F4; ++w)
-                    if (!GATHER || (w != 2 && w != 3)) nr[w] = src[w];
-            }
+            if (valid) {
+            const unsigned p = p_cur;
+            const float4 *nr = S.rec + j * RS_F4;
             float4 *sr = S.pk + j * PK_F4;
             const float4 r0 = nr[0], r1 = nr[1], r6 = nr[6], r7 = nr[7];
             float x[3] = {r0.x, r0.y, r0.z};
@@ -615,19 +681,29 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 sr[4] = make_float4(Ad[8], 0.f, 0.f, 0.f);
             }
             if (MODE != MODE_P2G) bin_end(D, ticket, p);
+            }
         }
 
-        if (SCATTER) {
-            if (SCAT == 1) {
-                // per-chunk fixed-point scales from the sums of the per-particle bounds
+        if (SCATTER && SCAT == 1) {
+            // per-chunk fixed-point scales from the sums of the per-particle bounds
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    bnd_m += __shfl_xor_sync(0xffffffffu, bnd_m, o);
-                    bnd_v += __shfl_xor_sync(0xffffffffu, bnd_v, o);
-                }
-                if ((tid & 31) == 0) { S.red[tid >> 5] = bnd_m; S.red[(TPB / 32) + (tid >> 5)] = bnd_v; }
+            for (int o = 16; o > 0; o >>= 1) {
+                bnd_m += __shfl_xor_sync(0xffffffffu, bnd_m, o);
+                bnd_v += __shfl_xor_sync(0xffffffffu, bnd_v, o);
             }
-            __syncthreads();
+            if ((tid & 31) == 0) { S.red[tid >> 5] = bnd_m; S.red[(TPB / 32) + (tid >> 5)] = bnd_v; }
+        }
+        // level 2 of chunk c + G has landed; phase A is done with the record and
+        // gather-tile buffers, so level 3 of chunk c + G goes in flight now
+        cp_async_wait_all();
+        __syncthreads();
+        if (has_next) {
+            if (SCATTER) stage_slots<TPB>(S, (kc + 1) & 1, ep_s);
+            stage_level3<TPB, GATHER>(D, S, S.cd[(kc + 1) % 3], gpar, ep_g);
+        }
+        cp_async_commit();
+
+        if (SCATTER) {
             if (SCAT == 1 && tid == 0) {
                 float bm = 0.f, bv = 0.f;
                 for (int w = 0; w < T / 32; ++w) { bm += S.red[w]; bv += S.red[(TPB / 32) + w]; }
@@ -689,8 +765,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                                 atomicAdd(&S.t.i[3 * ST3P + node], __float2int_rn(mm));
                             } else {
                                 const int I = ox - 1 + t0 + i, J = oy - 1 + t1 + jj, K = oz - 1 + t2 + k;
-                                const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 +
-                                                        ((K >> 2) - bz + 1)];
+                                const int sl = S.slot_s[kc & 1][(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 +
+                                                                ((K >> 2) - bz + 1)];
                                 if (sl >= 0)
                                     red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K), m0, m1,
                                                m2, mm);
@@ -717,16 +793,23 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                         if (mi == 0) mm = 0.f;
                         a0 = (float)S.t.i[q] * iv; a1 = (float)S.t.i[ST3P + q] * iv; a2 = (float)S.t.i[2 * ST3P + q] * iv;
                     }
+                    // cleared for the next chunk as it is read
+                    S.t.i[q] = 0; S.t.i[ST3P + q] = 0; S.t.i[2 * ST3P + q] = 0; S.t.i[3 * ST3P + q] = 0;
                     if (mm != 0.f) {
                         const int I = ox - 1 + i, J = oy - 1 + j, K = oz - 1 + k;
-                        const int sl = S.slot_s[(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 + ((K >> 2) - bz + 1)];
+                        const int sl = S.slot_s[kc & 1][(((I >> 2) - bx + 1) * 3 + ((J >> 2) - by + 1)) * 3 +
+                                                        ((K >> 2) - bz + 1)];
                         if (sl >= 0) red_add_v4(D.gmv[spar] + (size_t)sl * BLK_NODES + node_local(I, J, K), a0, a1, a2, mm);
                         else set_err(D, ERRB_CAPACITY);
                     }
                 }
             }
         }
+        // level 3 of chunk c + G has landed
+        cp_async_wait_all();
         __syncthreads();
+        if (!has_next) break;
+        c = cn;
     }
 }
 

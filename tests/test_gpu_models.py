@@ -67,7 +67,8 @@ def test_one_substep_further_models(orc, sim_mod):
     ref = orc.run(cfg, orc.new_state(sc.x, v, C, F), mat, 1)
     assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * np.abs(ref["v"]).max()
     assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
-    assert np.abs(got["C"] - ref["C"]).max() < 1e-5 * np.abs(ref["C"]).max()
+    # C = 4/dx^2 sum w v_i (x_i - x_p)^T inherits the grid-velocity error: |dC| <= (6/dx) max|dv|
+    assert np.abs(got["C"] - ref["C"]).max() < 6e-5 * np.abs(ref["v"]).max() / sc.dx
     assert np.abs(got["F"] - ref["F"]).max() < 2e-5
     # the Sigma clamp and the fluid projection both acted
     J = np.linalg.det(got["F"])
