@@ -85,6 +85,9 @@ def lib():
             L.orc_substep_adjoint.argtypes = [cp, ctypes.c_long, _P, mp, _P, _P, _P]
             L.orc_backward.argtypes = [cp, ctypes.c_long, mp, ctypes.c_int, _P, ctypes.c_int, _PI, _P, _P, _P]
             L.orc_covariance.argtypes = [ctypes.c_long, _P, _P, _P]
+            _PL = ctypes.POINTER(ctypes.c_long)
+            L.orc_mcis.argtypes = [ctypes.c_int, _PL, _P, _PL, _P, _PL, _P, ctypes.c_double, ctypes.c_double, _P, _P,
+                                   ctypes.POINTER(ctypes.c_longlong), _PL]
             L.orc_bgdo.argtypes = [cp, ctypes.c_long, ctypes.c_int, _P, mp, _PI, ctypes.c_int,
                                    ctypes.POINTER(_BgdoOpt), _P, _P, _P]
             _lib = L
@@ -385,3 +388,29 @@ def sym33(c):
     """(n,6) xx xy xz yy yz zz -> (n,3,3)."""
     c = np.asarray(c, dtype=np.float64).reshape(-1, 6)
     return np.stack([c[:, [0, 1, 2]], c[:, [1, 3, 4]], c[:, [2, 4, 5]]], axis=1)
+
+
+MCIS_WSCALE = 2.0 ** 40
+
+
+def mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma=0.02, eps=1e-6):
+    """MCIS steps 1-4 (§4.1) per object over contiguous ranges.  Returns
+    dict(d, w, cum (inclusive integer cumulative weights per object), picked
+    (global candidate index of every draw, -1 for an object without
+    candidates))."""
+    L = lib()
+    to_l = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.int64))
+    so, co, do = to_l(surf_off), to_l(cand_off), to_l(draw_off)
+    sf = _f64(surf, (-1, 3))
+    cf = _f64(cand, (-1, 3))
+    uu = _f64(u, (-1,))
+    n_obj = len(so) - 1
+    nc = int(co[-1])
+    d, w = np.zeros(nc), np.zeros(nc)
+    cum = np.zeros(nc, dtype=np.int64)
+    picked = np.zeros(int(do[-1]), dtype=np.int64)
+    PL = ctypes.POINTER(ctypes.c_long)
+    L.orc_mcis(n_obj, so.ctypes.data_as(PL), _d(sf), co.ctypes.data_as(PL), _d(cf), do.ctypes.data_as(PL), _d(uu),
+               float(sigma), float(eps), _d(d), _d(w), cum.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)),
+               picked.ctypes.data_as(PL))
+    return {"d": d, "w": w, "cum": cum, "picked": picked}

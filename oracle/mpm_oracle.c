@@ -1153,3 +1153,55 @@ void orc_covariance(long n, const double *F, const double *cov0, double *out) {
         o[0] = T[0]; o[1] = T[1]; o[2] = T[2]; o[3] = T[4]; o[4] = T[5]; o[5] = T[8];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* MCIS, Monte Carlo Importance Sampling of interior fill points (§4.1,     */
+/* steps 1-4).  Per object k (cluster C_k with candidates Q_k, given as      */
+/* contiguous ranges surf_off[k]..surf_off[k+1], cand_off[k]..cand_off[k+1]):*/
+/*   d_j = min_{c in C_k} |q_j - c|                     (step 1)             */
+/*   w_j = max(exp(-d_j^2 / (2 sigma^2)), eps)          (step 2)             */
+/*   p_j = w_j / sum_j' w_j'                            (step 3)             */
+/*   n_k i.i.d. draws with P(s = q_j) = p_j             (step 4)             */
+/* Readings: the draws are with replacement (each draw has the stated law); */
+/* draw i of object k takes the uniform u_i in [0, 1) given as input and     */
+/* returns the first candidate whose cumulative weight exceeds               */
+/* floor(u_i W_k), with the weights summed as integers w_j 2^40 rounded to   */
+/* nearest, so that the cumulative sums do not depend on summation order.   */
+/* Distances are exact: brute force over C_k in double precision.           */
+/* ------------------------------------------------------------------------ */
+
+#define MCIS_WSCALE 1099511627776.0   /* 2^40 */
+
+void orc_mcis(int n_obj, const long *surf_off, const double *surf, const long *cand_off, const double *cand,
+              const long *draw_off, const double *u, double sigma, double eps, double *d_out, double *w_out,
+              long long *cum_out, long *picked) {
+    for (int k = 0; k < n_obj; ++k) {
+        const long c0 = cand_off[k], nc = cand_off[k + 1] - cand_off[k];
+        long long *cum = (long long *)malloc((nc > 0 ? nc : 1) * sizeof(long long));
+        long long total = 0;
+        for (long j = 0; j < nc; ++j) {
+            const double *q = cand + 3 * (c0 + j);
+            double best = INFINITY;
+            for (long c = surf_off[k]; c < surf_off[k + 1]; ++c) {
+                double e0 = q[0] - surf[3 * c], e1 = q[1] - surf[3 * c + 1], e2 = q[2] - surf[3 * c + 2];
+                double d2 = e0 * e0 + e1 * e1 + e2 * e2;
+                if (d2 < best) best = d2;
+            }
+            double w = exp(-best / (2.0 * sigma * sigma));
+            if (w < eps) w = eps;
+            total += (long long)floor(w * MCIS_WSCALE + 0.5);   /* round half up: exact for w <= 1 */
+            cum[j] = total;
+            if (d_out) d_out[c0 + j] = sqrt(best);
+            if (w_out) w_out[c0 + j] = w;
+            if (cum_out) cum_out[c0 + j] = total;
+        }
+        for (long i = draw_off[k]; i < draw_off[k + 1]; ++i) {
+            if (nc == 0) { picked[i] = -1; continue; }
+            const long long t = (long long)floor(u[i] * (double)total);
+            long j = 0;
+            while (j < nc - 1 && cum[j] <= t) ++j;     /* first cumulative weight above t */
+            picked[i] = c0 + j;
+        }
+        free(cum);
+    }
+}
