@@ -247,6 +247,34 @@ MPM_API mpm_status mpm_load_covariance(mpm_ctx *ctx, const float *cov0, void *st
  * Enqueued on the stream; does not synchronise. */
 MPM_API mpm_status mpm_get_covariance(mpm_ctx *ctx, float *cov, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * MCIS interior fill sampling (§4.1 "Monte Carlo Importance Sampling",
+ * steps 1-4).  Independent of any context.  Object k owns surface points
+ * surf[surf_off[k] .. surf_off[k+1]) (its cluster C_k), candidate points
+ * cand[cand_off[k] .. cand_off[k+1]) (Q_k, already inside the object) and
+ * draws draw_off[k] .. draw_off[k+1]:
+ *     d_j = min_{c in C_k} |q_j - c|                       (step 1)
+ *     w_j = max(exp(-d_j^2 / (2 sigma^2)), eps)            (step 2; the paper
+ *                                                            uses sigma 0.02, eps 1e-6)
+ *     p_j = w_j / sum w                                    (step 3)
+ *     draw i: P(candidate j) = p_j, independent draws       (step 4)
+ * Draw i takes the uniform u[i] in [0, 1) and returns the global index of
+ * the first candidate of its object whose cumulative weight exceeds
+ * floor(u_i W_k), the weights summed as integers floor(w 2^40 + 1/2).
+ * Distances are exact (FP64) up to d_cut = sigma sqrt(2 ln(1/eps)); beyond
+ * it the weight is eps and d may be larger than the true distance (INFINITY
+ * when nothing lies within d_cut).  Coordinates are expected in the unit
+ * cube (App. C.1).  Offsets are host arrays of n_obj + 1 int64 starting at
+ * 0; surf, cand (n x 3 float), u (double) and the outputs d, w (n_cand
+ * double, nullable) and picked (n_draw int64; -1 for an object without
+ * candidates) may be host or device.  Synchronises the stream.  The message
+ * of a failure is mpm_mcis_last_error().
+ * ------------------------------------------------------------------------ */
+MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, const float *surf, const int64_t *cand_off,
+                            const float *cand, const int64_t *draw_off, const double *u, float sigma, float eps,
+                            double *d, double *w, int64_t *picked, void *stream);
+MPM_API const char *mpm_mcis_last_error(void);
+
 /* Diagnostic: P2G of the current state into dense device arrays m
  * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at
  * ((b * R0 + I) * R1 + J) * R2 + K) and mv (3 floats per node); the particle

@@ -70,6 +70,9 @@ SIGNATURES = {
                                 _vp, _vp]),
     "mpm_load_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
     "mpm_get_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
+    "mpm_mcis": (ctypes.c_int, [ctypes.c_int32, _i64p, _vp, _i64p, _vp, _i64p, _vp, ctypes.c_float, ctypes.c_float,
+                                _vp, _vp, _vp, _vp]),
+    "mpm_mcis_last_error": (ctypes.c_char_p, []),
     "mpm_set_tuning": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mpm_autotune": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, _vp]),
     "mpm_substep_noalloc": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
@@ -217,3 +220,13 @@ def mpm_load_covariance(ctx, cov0, stream):
 
 def mpm_get_covariance(ctx, cov, stream):
     check(lib().mpm_get_covariance(ctx, cov, stream), ctx)
+
+
+def mpm_mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma, eps, d, w, picked, stream):
+    n_obj = len(surf_off) - 1
+    so = (ctypes.c_int64 * len(surf_off))(*[int(v) for v in surf_off])
+    co = (ctypes.c_int64 * len(cand_off))(*[int(v) for v in cand_off])
+    do = (ctypes.c_int64 * len(draw_off))(*[int(v) for v in draw_off])
+    st = lib().mpm_mcis(n_obj, so, surf, co, cand, do, u, float(sigma), float(eps), d, w, picked, stream)
+    if st != 0:
+        raise MpmError(st, (lib().mpm_mcis_last_error() or b"").decode())

@@ -421,3 +421,33 @@ def gaussian_covariances(sc: Scene, k_seed=50):
     M = R * s[:, None, :]
     S = M @ M.transpose(0, 2, 1)
     return _f32(np.stack([S[:, 0, 0], S[:, 0, 1], S[:, 0, 2], S[:, 1, 1], S[:, 1, 2], S[:, 2, 2]], 1))
+
+
+def mcis_case(n_surface=(36_000, 36_000, 36_000), n_cand=(250_000, 250_000, 250_000),
+              n_draw=(64_000, 64_000, 64_000), k_seed=70):
+    """Inputs of the MCIS fill (§4.1) for the three objects of the 300k scene:
+    per object its surface proxy C_k (uniform surface samples with a normal
+    offset N(0, (0.1 dx)^2), dx = 1/128, like the splat shells), candidates
+    uniform in its bounding box kept where the shape's own inside test holds
+    (a stand-in for the occupancy selection, which precedes MCIS), and one
+    uniform in [0, 1) per draw.  Returns dict(surf_off, surf, cand_off, cand,
+    draw_off, u)."""
+    rng = _rng(k_seed)
+    dx = 1.0 / 128
+    shapes = [Sphere((0.2, 0.20, 0.5), 0.10), Torus((0.5, 0.14, 0.5), 0.10, 0.04), Box((0.8, 0.18, 0.5), 0.08)]
+    surf, cand = [], []
+    for k, sh in enumerate(shapes):
+        surf.append(_shell(sh, n_surface[k], 0.1 * dx, rng))
+        lo, hi = sh.bbox()
+        got = []
+        need = n_cand[k]
+        while need > 0:
+            q = lo + (hi - lo) * rng.random((2 * need + 64, 3))
+            q = q[sh.inside(q)][:need]
+            got.append(q)
+            need -= len(q)
+        cand.append(np.concatenate(got))
+    off = lambda parts: np.concatenate([[0], np.cumsum([len(a) for a in parts])]).astype(np.int64)
+    return {"surf_off": off(surf), "surf": _f32(np.concatenate(surf)), "cand_off": off(cand),
+            "cand": _f32(np.concatenate(cand)), "draw_off": np.concatenate([[0], np.cumsum(n_draw)]).astype(np.int64),
+            "u": rng.random(int(sum(n_draw)))}

@@ -211,3 +211,19 @@ class Trajectory(torch.autograd.Function):
 
 def trajectory(params, sim, init, frame_sub):
     return Trajectory.apply(params, sim, init, frame_sub)
+
+
+def mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma=0.02, eps=1e-6, device="cuda", stream=None):
+    """MCIS fill sampling (§4.1 steps 1-4) on the GPU: objects as contiguous
+    ranges (offsets of n_obj + 1), uniforms u per draw.  Returns dict(d, w,
+    picked) as device tensors (float64, float64, int64)."""
+    dv = torch.device(device)
+    surf = _dev(surf, torch.float32, dv, 3)
+    cand = _dev(cand, torch.float32, dv, 3)
+    u = _dev(u, torch.float64, dv)
+    nc, nd = int(cand_off[-1]), int(draw_off[-1])
+    out = {"d": torch.empty(nc, dtype=torch.float64, device=dv), "w": torch.empty(nc, dtype=torch.float64, device=dv),
+           "picked": torch.empty(nd, dtype=torch.int64, device=dv)}
+    L.mpm_mcis(surf_off, _p(surf), cand_off, _p(cand), draw_off, _p(u), sigma, eps, _p(out["d"]), _p(out["w"]),
+               _p(out["picked"]), _stream(stream))
+    return out
