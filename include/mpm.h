@@ -271,7 +271,7 @@ MPM_API mpm_status mpm_get_covariance(mpm_ctx *ctx, float *cov, void *stream);
  * of a failure is mpm_mcis_last_error().
  * ------------------------------------------------------------------------ */
 MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, const float *surf, const int64_t *cand_off,
-                            const float *cand, const int64_t *draw_off, const double *u, float sigma, float eps,
+                            const float *cand, const int64_t *draw_off, const double *u, double sigma, double eps,
                             double *d, double *w, int64_t *picked, void *stream);
 MPM_API const char *mpm_mcis_last_error(void);
 

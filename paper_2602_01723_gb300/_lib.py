@@ -70,7 +70,7 @@ SIGNATURES = {
                                 _vp, _vp]),
     "mpm_load_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
     "mpm_get_covariance": (ctypes.c_int, [_ctx_p, _vp, _vp]),
-    "mpm_mcis": (ctypes.c_int, [ctypes.c_int32, _i64p, _vp, _i64p, _vp, _i64p, _vp, ctypes.c_float, ctypes.c_float,
+    "mpm_mcis": (ctypes.c_int, [ctypes.c_int32, _i64p, _vp, _i64p, _vp, _i64p, _vp, ctypes.c_double, ctypes.c_double,
                                 _vp, _vp, _vp, _vp]),
     "mpm_mcis_last_error": (ctypes.c_char_p, []),
     "mpm_set_tuning": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),

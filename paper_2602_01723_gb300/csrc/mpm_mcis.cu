@@ -174,13 +174,46 @@ __global__ void k_mc_scan_i64_add(long long *out, long long n, const long long *
     if (i < n) out[i] += totals[blockIdx.x];
 }
 
+// candidates in (object, cell) order, so that the threads of a warp search
+// the same cells
+__global__ void k_mc_cand_count(int n_obj, const int64_t *coff, const float *cand, Grid g, unsigned *cnt,
+                                unsigned *rank) {
+    const int64_t n = coff[n_obj];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int k = find_range(coff, n_obj, j);
+        const long long key = (long long)k * g.cells +
+                              ((long long)cell_of(cand[3 * j], g.inv_h, g.G) * g.G + cell_of(cand[3 * j + 1], g.inv_h, g.G)) *
+                                  g.G + cell_of(cand[3 * j + 2], g.inv_h, g.G);
+        rank[j] = atomicAdd(&cnt[key], 1u);
+    }
+}
+__global__ void k_mc_cand_scatter(int n_obj, const int64_t *coff, const float *cand, Grid g, const unsigned *start,
+                                  const unsigned *rank, unsigned *order) {
+    const int64_t n = coff[n_obj];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int k = find_range(coff, n_obj, j);
+        const long long key = (long long)k * g.cells +
+                              ((long long)cell_of(cand[3 * j], g.inv_h, g.G) * g.G + cell_of(cand[3 * j + 1], g.inv_h, g.G)) *
+                                  g.G + cell_of(cand[3 * j + 2], g.inv_h, g.G);
+        order[start[key] + rank[j]] = (unsigned)j;
+    }
+}
+
+// squared distance from q to the box of cell c (cells of edge h from the origin)
+__device__ __forceinline__ double box_d2(double q, int c, double h) {
+    const double lo = c * h, hi = lo + h;
+    const double e = q < lo ? lo - q : (q > hi ? q - hi : 0.0);
+    return e * e;
+}
+
 // steps 1 and 2 per candidate: exact nearest-surface distance within d_cut, weight
-__global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, Grid g, const unsigned *start,
-                        const unsigned *cnt, const float4 *sorted, double sigma, double eps, double *d,
-                        double *w, long long *wq) {
+__global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, const unsigned *order, Grid g,
+                        const unsigned *start, const unsigned *cnt, const float4 *sorted, double sigma, double eps,
+                        double *d, double *w, long long *wq) {
     const int64_t n = coff[n_obj];
     const double h = 1.0 / (double)g.inv_h;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = order[t];
         const int k = find_range(coff, n_obj, j);
         const float qx = cand[3 * j], qy = cand[3 * j + 1], qz = cand[3 * j + 2];
         const int cx = cell_of(qx, g.inv_h, g.G), cy = cell_of(qy, g.inv_h, g.G), cz = cell_of(qz, g.inv_h, g.G);
@@ -200,6 +233,11 @@ __global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, Grid 
                         if (max(abs(ix), max(abs(iy), abs(iz))) != r) continue;   // ring r only
                         const int z = cz + iz;
                         if (z < 0 || z >= g.G) continue;
+                        // a cell wholly farther than the best point holds nothing closer
+                        // (cells are clamped at the cube's faces, so only interior cells are skipped)
+                        if (x > 0 && y > 0 && z > 0 && x < g.G - 1 && y < g.G - 1 && z < g.G - 1 &&
+                            box_d2(qx, x, h) + box_d2(qy, y, h) + box_d2(qz, z, h) > best)
+                            continue;
                         const long long key = base + ((long long)x * g.G + y) * g.G + z;
                         const unsigned s0 = start[key], s1 = s0 + cnt[key];
                         for (unsigned s = s0; s < s1; ++s) {
@@ -265,10 +303,10 @@ int blocks_for(long long n, int t) {
 
 extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, const float *surf,
                                        const int64_t *cand_off, const float *cand, const int64_t *draw_off,
-                                       const double *u, float sigma, float eps, double *d, double *w,
+                                       const double *u, double sigma, double eps, double *d, double *w,
                                        int64_t *picked, void *stream) {
     g_mcis_msg.clear();
-    if (n_obj < 1 || !surf_off || !cand_off || !draw_off || !(sigma > 0.f) || !(eps > 0.f) || !(eps < 1.f)) {
+    if (n_obj < 1 || !surf_off || !cand_off || !draw_off || !(sigma > 0.0) || !(eps > 0.0) || !(eps < 1.0)) {
         g_mcis_msg = "mcis: n_obj >= 1, offsets non-NULL, sigma > 0, 0 < eps < 1";
         return MPM_ERR_INVALID_ARG;
     }
@@ -287,7 +325,7 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
         return MPM_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const double cut = (double)sigma * std::sqrt(2.0 * std::log(1.0 / (double)eps));
+    const double cut = sigma * std::sqrt(2.0 * std::log(1.0 / eps));
     Grid g;
     // cell edge 1/G >= d_cut / RINGS, so rings 0..RINGS hold every point within d_cut
     g.G = (int)std::floor(RINGS / cut);
@@ -311,6 +349,10 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
     const size_t o_cnt = off; off += al(keys * 4);
     const size_t o_start = off; off += al(keys * 4);
     const size_t o_rank = off; off += al(ns * 4);
+    const size_t o_cnt2 = off; off += al(keys * 4);
+    const size_t o_start2 = off; off += al(keys * 4);
+    const size_t o_crank = off; off += al(nc * 4);
+    const size_t o_order = off; off += al(nc * 4);
     const size_t o_sorted = off; off += al(ns * 16);
     const size_t o_wq = off; off += al(nc * 8);
     const size_t o_cum = off; off += al(nc * 8);
@@ -345,6 +387,7 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
         if (nc > 0 && !is_dev(cand)) { MC_CK(cudaMemcpyAsync(P(o_cand), cand, nc * 12, cudaMemcpyHostToDevice, st)); dcand = (const float *)P(o_cand); }
         if (nd > 0 && !is_dev(u)) { MC_CK(cudaMemcpyAsync(P(o_u), u, nd * 8, cudaMemcpyHostToDevice, st)); du = (const double *)P(o_u); }
         unsigned *cnt = (unsigned *)P(o_cnt), *start = (unsigned *)P(o_start), *rank = (unsigned *)P(o_rank);
+        unsigned *cnt2 = (unsigned *)P(o_cnt2), *start2 = (unsigned *)P(o_start2);
         float4 *sorted = (float4 *)P(o_sorted);
         long long *wq = (long long *)P(o_wq), *cum = (long long *)P(o_cum), *tot = (long long *)P(o_tot);
         MC_CK(cudaMemsetAsync(cnt, 0, keys * 4, st));
@@ -362,8 +405,14 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
         double *dw = w && is_dev(w) ? w : (double *)P(o_w);
         int64_t *dp = picked && is_dev(picked) ? picked : (int64_t *)P(o_pick);
         if (nc > 0) {
-            k_mc_nn<<<blocks_for(nc, 128), 128, 0, st>>>(n_obj, dcoff, dcand, g, start, cnt, sorted, (double)sigma,
-                                                           (double)eps, dd, dw, wq);
+            unsigned *crank = (unsigned *)P(o_crank), *order = (unsigned *)P(o_order);
+            MC_CK(cudaMemsetAsync(cnt2, 0, keys * 4, st));
+            k_mc_cand_count<<<blocks_for(nc, 256), 256, 0, st>>>(n_obj, dcoff, dcand, g, cnt2, crank);
+            k_mc_scan_u32<<<1, 1024, 0, st>>>(cnt2, start2, keys);
+            k_mc_cand_scatter<<<blocks_for(nc, 256), 256, 0, st>>>(n_obj, dcoff, dcand, g, start2, crank, order);
+            MC_CK(cudaGetLastError());
+            k_mc_nn<<<blocks_for(nc, 128), 128, 0, st>>>(n_obj, dcoff, dcand, order, g, start, cnt, sorted, sigma, eps,
+                                                           dd, dw, wq);
             MC_CK(cudaGetLastError());
             k_mc_scan_i64_block<<<(unsigned)nb, 1024, 0, st>>>(wq, cum, nc, tot);
             k_mc_scan_i64_totals<<<1, 1024, 0, st>>>(tot, nb);
