@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
+#include <vector>
 #include <string>
 
 #include "mpm_internal.h"
@@ -773,12 +775,30 @@ __global__ void k_adj_clear(Dev D, float4 *gbar) {
 }
 
 // adjoint of positions += dL/dx of one frame
-__global__ void k_inject(int n, float4 *adj, const float *dLdx) {
+// the current segment of the reverse pass, read by k_inject_tab
+struct SegParams {
+    const float *dldx;     // n_frames x n x 3
+    long long s0;          // first substep of the segment
+};
+__global__ void k_set_seg(SegParams *sp, const float *dldx, long long s0) {
+    sp->dldx = dldx;
+    sp->s0 = s0;
+}
+// adds the loss gradient of every frame taken after substep s0 + j + 1
+__global__ void k_inject_tab(int n, float4 *adj, const int *frame_first, const int *frame_next, const SegParams *sp,
+                             int j) {
+    const long long sub = sp->s0 + j + 1;
+    int f = frame_first[sub];
+    if (f < 0) return;
+    const float *base = sp->dldx;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         float4 a = adj[(size_t)p * ADJ_F4];
-        a.x += dLdx[3 * p];
-        a.y += dLdx[3 * p + 1];
-        a.z += dLdx[3 * p + 2];
+        for (int g = f, guard = 0; g >= 0 && guard < 1 << 20; g = frame_next[g], ++guard) {
+            const float *dl = base + (size_t)g * n * 3;
+            a.x += dl[3 * p];
+            a.y += dl[3 * p + 1];
+            a.z += dl[3 * p + 2];
+        }
         adj[(size_t)p * ADJ_F4] = a;
     }
 }
@@ -810,6 +830,11 @@ void free_adjoint(AdjointStore &a) {
     if (a.gbar) cudaFree(a.gbar);
     if (a.frames) cudaFree(a.frames);
     if (a.final_state) cudaFree(a.final_state);
+    if (a.frame_first) cudaFree(a.frame_first);
+    if (a.frame_next) cudaFree(a.frame_next);
+    if (a.seg) cudaFree(a.seg);
+    for (int e = 0; e < 2; ++e)
+        if (a.seg_graph[e]) cudaGraphExecDestroy(a.seg_graph[e]);
     a = AdjointStore();
 }
 
@@ -894,6 +919,79 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     D.rec = saved;
 }
 
+// One segment of the reverse pass on the checkpoint already in D.rec (whose
+// binning is the pending one): tape the segment's input states by one
+// forward pass, then reverse its substeps from the last, injecting frame
+// gradients from the device table.  Leaves the adjoint in adj[cur ^ (len & 1)].
+static mpm_status segment_body(mpm_ctx *ctx, int len, int cur, int pg, cudaStream_t st) {
+    Dev &D = ctx->D;
+    AdjointStore &A = ctx->adj;
+    const size_t n = (size_t)D.n;
+    rebin(ctx, st);
+    if (cudaMemcpyAsync(A.tape, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
+    mpm_status s;
+    if (len > 1 && (s = run_substeps(ctx, len - 1, st, A.tape, (size_t)ctx->cap * REC_F4))) return s;
+    for (int j = len - 1; j >= 0; --j) {
+        k_inject_tab<<<pg, 256, 0, st>>>((int)n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j);
+        ++ctx->launches;
+        adjoint_substep(ctx, A.tape + (size_t)j * ctx->cap * REC_F4, A.adj[cur], A.adj[cur ^ 1], st);
+        cur ^= 1;
+    }
+    return MPM_OK;
+}
+
+// the segment as a CUDA graph, captured on the library's own stream the first
+// time a segment of this length and adjoint parity runs with these buffers
+static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, long long &launches) {
+    AdjointStore &A = ctx->adj;
+    const long long key[4] = {(long long)len * 2 + cur, (long long)ctx->D.n * 1000003ll + ctx->generation,
+                              (long long)(uintptr_t)A.tape ^ (long long)(uintptr_t)A.gbar,
+                              (long long)(uintptr_t)A.adj[0] ^ ((long long)(uintptr_t)A.frame_first << 1)};
+    ++A.seg_clock;
+    for (int e = 0; e < 2; ++e)
+        if (A.seg_graph[e] && std::equal(key, key + 4, A.seg_key[e])) {
+            A.seg_used[e] = A.seg_clock;
+            launches = A.seg_launches[e];
+            return A.seg_graph[e];
+        }
+    const int e = A.seg_used[0] <= A.seg_used[1] ? 0 : 1;   // least recently used entry
+    if (A.seg_graph[e]) { cudaGraphExecDestroy(A.seg_graph[e]); A.seg_graph[e] = nullptr; }
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->cap_stream = nullptr;
+        return nullptr;
+    }
+    const long long l0 = ctx->launches;
+    const bool pend = ctx->bins_pending;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const mpm_status s = segment_body(ctx, len, cur, pg, ctx->cap_stream);
+    if (cudaStreamEndCapture(ctx->cap_stream, &g) != cudaSuccess || !g || s) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        ctx->launches = l0;
+        ctx->bins_pending = pend;
+        return nullptr;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) { cudaGetLastError(); ex = nullptr; }
+    cudaGraphDestroy(g);
+    launches = ctx->launches - l0;        // kernels one replay launches
+    ctx->launches = l0;                   // capture launched nothing
+    ctx->bins_pending = pend;             // replays start from this state
+    if (ex) {
+        A.seg_graph[e] = ex;
+        A.seg_launches[e] = launches;
+        A.seg_used[e] = A.seg_clock;
+        std::copy(key, key + 4, A.seg_key[e]);
+    }
+    return ex;
+}
+
 }  // namespace mpm
 
 using namespace mpm;
@@ -952,35 +1050,64 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         cudaMemsetAsync(A.adj[0], 0, n * ADJ_F4 * sizeof(float4), st) != cudaSuccess ||
         cudaMemsetAsync(A.gpar, 0, n * sizeof(float4), st) != cudaSuccess)
         return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
+    // frame table: per substep the first frame taken after it, per frame the next one there
+    if (A.frame_first_cap < S + 1) {
+        if ((s = dev_alloc(ctx, &A.frame_first, (size_t)S + 1))) { A.frame_first_cap = 0; return s; }
+        A.frame_first_cap = S + 1;
+    }
+    if (A.frame_cap < std::max(n_frames, 1)) {
+        if ((s = dev_alloc(ctx, &A.frame_next, (size_t)std::max(n_frames, 1)))) { A.frame_cap = 0; return s; }
+        A.frame_cap = std::max(n_frames, 1);
+    }
+    if (!A.seg) {
+        if (cudaMalloc(&A.seg, sizeof(SegParams)) != cudaSuccess) {
+            cudaGetLastError();
+            A.seg = nullptr;
+            return ctx_fail(ctx, MPM_ERR_OOM, "reverse-pass allocation failed");
+        }
+    }
+    {
+        std::vector<int> first((size_t)S + 1, -1), next((size_t)std::max(n_frames, 1), -1);
+        for (int f = n_frames - 1; f >= 0; --f) {
+            next[f] = first[frame_substep[f]];
+            first[frame_substep[f]] = f;
+        }
+        // pageable host memory: the copies complete before cudaMemcpyAsync returns
+        if (cudaMemcpyAsync(A.frame_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemcpyAsync(A.frame_next, next.data(), next.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "frame table copy");
+    }
     int cur = 0;
     const int pg = grid_for((long long)n, 256);
-    auto inject = [&](long long sub) {
-        for (int f = 0; f < n_frames; ++f)
-            if (frame_substep[f] == sub) {
-                k_inject<<<pg, 256, 0, st>>>((int)n, A.adj[cur], dldx + (size_t)f * n * 3);
-                ++ctx->launches;
-            }
-    };
     const long long nseg = (S + k - 1) / k;
     for (long long c = nseg - 1; c >= 0; --c) {
         const long long s0 = c * k;
         const int len = (int)std::min<long long>(k, S - s0);
-        // recompute the segment's input states
+        // the segment's input state, its pending binning consumed here so that
+        // every segment starts from the same host-side state
         if (cudaMemcpyAsync(D.rec, A.ckpt[(size_t)c], n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
             return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
-        rebin(ctx, st);
-        if (cudaMemcpyAsync(A.tape, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
-        // one pipelined forward over the segment, copying each substep's result to the tape
-        if (len > 1 && (s = run_substeps(ctx, len - 1, st, A.tape, (size_t)ctx->cap * REC_F4))) return s;
-        // reverse through the segment
-        for (int j = len - 1; j >= 0; --j) {
-            inject(s0 + j + 1);
-            adjoint_substep(ctx, A.tape + (size_t)j * ctx->cap * REC_F4, A.adj[cur], A.adj[cur ^ 1], st);
-            cur ^= 1;
+        if (ctx->bins_pending) L_plan(ctx, 0, st);
+        k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, s0);
+        ++ctx->launches;
+        long long per = 0;
+        cudaGraphExec_t ex = (ctx->use_graph && !ctx->trace_on) ? segment_graph(ctx, len, cur, pg, per) : nullptr;
+        if (ex) {
+            if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+                cudaGetLastError();
+                return ctx_fail(ctx, MPM_ERR_CUDA, "segment graph launch failed");
+            }
+            ctx->launches += per;
+            ctx->bins_pending = false;    // the segment ends with its plan consumed
+        } else if ((s = segment_body(ctx, len, cur, pg, st))) {
+            return s;
         }
+        cur ^= (len & 1);
     }
-    inject(0);
+    // frames taken at substep 0
+    k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, -1);
+    k_inject_tab<<<pg, 256, 0, st>>>((int)n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, 0);
+    ctx->launches += 2;
     // outputs
     float *dp = dL_dparams, *ds = dL_dstate0;
     const bool dp_dev = is_device_ptr(dL_dparams), ds_dev = !dL_dstate0 || is_device_ptr(dL_dstate0);

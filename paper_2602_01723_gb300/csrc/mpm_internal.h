@@ -56,6 +56,21 @@ struct AdjointStore {
     long long cap_adj = 0;          // particle capacity of adj / gpar / final_state
     long long tape_cap = 0;         // particle capacity of the tape
     unsigned pool = 0;              // grid-adjoint pool capacity (blocks)
+    // frame injection driven from device memory (so that one captured
+    // segment graph serves every segment): per substep the first frame
+    // adjoint to add, per frame the next one at the same substep, and the
+    // current segment's first substep and dL/dx base
+    int *frame_first = nullptr;     // recorded substeps + 1 entries
+    int *frame_next = nullptr;      // frames
+    long long frame_cap = 0, frame_first_cap = 0;
+    void *seg = nullptr;            // device SegParams
+    // CUDA graph of one segment's recompute + reverse, keyed by its shape
+    // (a full segment and a shorter last one: two entries, least recently used replaced)
+    cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
+    long long seg_key[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    long long seg_launches[2] = {0, 0};   // kernels one replay launches
+    long long seg_used[2] = {0, 0};
+    long long seg_clock = 0;
 };
 void free_adjoint(AdjointStore &a);
 
