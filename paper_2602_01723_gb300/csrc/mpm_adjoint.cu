@@ -389,24 +389,88 @@ __device__ __forceinline__ void unpack_particle(const float4 r[REC_F4], Particle
 constexpr int GTP = GT + 1;                  // padded row of the fixed-point tile
 constexpr int GT3P = GT * GT * GTP;
 __device__ __forceinline__ int gidx(int i, int j, int k) { return (i * GT + j) * GTP + k; }
+constexpr int AS_F4 = 13;                   // staged stride: record words 0,1,4..7 (6) + adjoint (6), odd
 struct AdjG2PSmem {
+    float4 st[ADJ_THREADS * AS_F4];          // staged record and adjoint of the chunk's particles
     float4 g[GT3];                           // grid velocity tile (v, m)
     int t[3 * GT3P];                         // fixed-point grid-velocity adjoint, component-major
     float4 pk[ADJ_THREADS * 4];              // packets: f(3) - | vt(3) - | Ct(9) ...
-    int slot[8];
+    int4 cd[3];                              // chunk descriptors, ring of (c, c + G, c + 2G)
+    unsigned pidx[ADJ_THREADS];              // sorted indices of the next chunk
+    unsigned pe[8];                          // page words of the next chunk's 8 tile blocks
+    int ps[8];
+    int slot[2][8];                          // pool slots of the tile blocks, per chunk parity
     float red[ADJ_THREADS / 32];
     float scale;
 };
 
+__device__ __forceinline__ unsigned a_smem(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void a_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void a_cp4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(a_smem(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void a_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void a_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// level 2 of a chunk: sorted indices and the page words of its 8 tile blocks
+template <typename SM>
+__device__ __forceinline__ void adj_stage2(const Dev &D, SM &S, int4 ch, unsigned ep) {
+    const int tid = threadIdx.x;
+    if (tid < ch.z) a_cp4(&S.pidx[tid], D.sorted + ch.y + tid);
+    const int t = tid - 64;   // lookups on the third warp
+    if (t >= 0 && t < 8) {
+        int inst, bx, by, bz;
+        key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
+        const int qx = bx + (t >> 2), qy = by + ((t >> 1) & 1), qz = bz + (t & 1);
+        if (qx >= D.NB[0] || qy >= D.NB[1] || qz >= D.NB[2]) {
+            S.pe[t] = ep + 1u;
+            S.ps[t] = -1;
+        } else {
+            const unsigned k = block_key(D, inst, qx, qy, qz);
+            a_cp4(&S.pe[t], D.page_epoch[0] + k);
+            a_cp4(&S.ps[t], D.page[0] + k);
+        }
+    }
+}
+// level 3: records and adjoints (instruction w of a warp: float4 l % 8 of particles 4 w + l / 8)
+// and the gather tile; needs the level-2 words in shared memory
+__device__ __forceinline__ void adj_stage3(const Dev &D, AdjG2PSmem &S, int4 ch, const float4 *ain, int buf,
+                                           unsigned ep) {
+    const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31, piece = lane & 7;
+    if (tid < 8) S.slot[buf][tid] = S.pe[tid] == ep ? S.ps[tid] : -1;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int j = wbase + 4 * w + (lane >> 3);
+        if (j < ch.z) {
+            const size_t p = S.pidx[j];
+            if (piece != 2 && piece != 3)
+                a_cp16(&S.st[j * AS_F4 + (piece < 2 ? piece : piece - 2)], D.rec + p * REC_F4 + piece);
+            if (piece < ADJ_F4) a_cp16(&S.st[j * AS_F4 + 6 + piece], ain + p * ADJ_F4 + piece);
+        }
+    }
+    for (int t = tid; t < GT3; t += ADJ_THREADS) {
+        const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+        const int b = ((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2);
+        const int sl = S.pe[b] == ep ? S.ps[b] : -1;
+        if (sl >= 0) a_cp16(&S.g[t], D.gv[0] + (size_t)sl * BLK_NODES + node_loc(i, j, k));
+        else S.g[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // Reverse of G2P, advection, F update and return map for the particles of
-// one chunk per iteration.  Phase A (one particle per thread, record and
-// adjoint loaded into registers after one round trip for the sorted index):
-// recompute v', C', G = (I + dt C') F; reverse the return map, the F update
-// and advection; accumulate the position adjoint of the gathers; leave a
-// packet (position in the tile, vbar_tot, Cbar_tot).  Phase B: scatter the
-// grid-velocity adjoint wt (vbar_tot + 4/dx^2 Cbar_tot (x_i - x_p)) into an
-// int32 fixed-point tile (per-chunk scale 2^30 / sum of per-particle bounds)
-// and flush it with one vector reduction per touched node.
+// one chunk per iteration, software-pipelined over the chunks a CTA owns:
+// the next chunk's indices and page words (level 2, in flight during phase
+// A) and its records, adjoints and grid-velocity tile (level 3, in flight
+// during phase B and the flush) arrive by cp.async.  Phase A (one particle
+// per thread): recompute v', C', G = (I + dt C') F; reverse the return map,
+// the F update and advection; accumulate the position adjoint of the
+// gathers; leave a packet (position in the tile, vbar_tot, Cbar_tot).  Phase
+// B: scatter the grid-velocity adjoint wt (vbar_tot + 4/dx^2 Cbar_tot
+// (x_i - x_p)) into an int32 fixed-point tile (per-chunk scale 2^30 / sum of
+// per-particle bounds) and flush it with one vector reduction per touched
+// node.
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
                                                          float4 *gpar, float4 *gbar) {
     __shared__ AdjG2PSmem S;
@@ -415,40 +479,42 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
     const float c4 = 4.f * inv_dx * inv_dx;
     const int tid = threadIdx.x;
-    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-        const int4 ch = D.chunks[c];
+    unsigned c = blockIdx.x;
+    if (c >= n_chunks) return;
+    // prologue: descriptors of c and c + G, levels 2 and 3 of chunk c
+    if (tid == 0) {
+        S.cd[0] = D.chunks[c];
+        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+    }
+    for (int t = tid; t < 3 * GT3P; t += ADJ_THREADS) S.t[t] = 0;
+    __syncthreads();
+    adj_stage2(D, S, S.cd[0], ep);
+    a_commit();
+    a_wait();
+    __syncthreads();
+    adj_stage3(D, S, S.cd[0], ain, 0, ep);
+    a_commit();
+    a_wait();
+    __syncthreads();
+    for (int kc = 0;; ++kc) {
+        const int4 ch = S.cd[kc % 3];
         const int cnt = min(ch.z, ADJ_THREADS);
+        const unsigned cn = c + gridDim.x;
+        const bool has_next = cn < n_chunks;
+        const bool valid = tid < cnt;
+        const unsigned p = valid ? S.pidx[tid] : 0u;   // read before level 2 of c + G overwrites it
+        if (tid == 0 && cn + gridDim.x < n_chunks) a_cp16(&S.cd[(kc + 2) % 3], D.chunks + cn + gridDim.x);
+        if (has_next) adj_stage2(D, S, S.cd[(kc + 1) % 3], ep);
+        a_commit();
         int inst, bx, by, bz;
         key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
-        const bool valid = tid < cnt;
-        const unsigned p = valid ? D.sorted[ch.y + tid] : 0u;
-        if (tid < 8) S.slot[tid] = page_slot_a(D, 0, ep, inst, bx + (tid >> 2), by + ((tid >> 1) & 1), bz + (tid & 1));
-        for (int t = tid; t < 3 * GT3P; t += ADJ_THREADS) S.t[t] = 0;
-        __syncthreads();
         float4 rr[REC_F4], aa[ADJ_F4];
         if (valid) {
+            const float4 *q = S.st + tid * AS_F4;
+            rr[0] = q[0]; rr[1] = q[1]; rr[4] = q[2]; rr[5] = q[3]; rr[6] = q[4]; rr[7] = q[5];
 #pragma unroll
-            for (int w = 0; w < REC_F4; ++w) if (w != 2 && w != 3) rr[w] = D.rec[(size_t)p * REC_F4 + w];
-#pragma unroll
-            for (int w = 0; w < ADJ_F4; ++w) aa[w] = ain[(size_t)p * ADJ_F4 + w];
+            for (int w = 0; w < ADJ_F4; ++w) aa[w] = q[6 + w];
         }
-        {
-            float4 gt[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int t = tid + u * ADJ_THREADS;
-                gt[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (t < GT3) {
-                    const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
-                    const int sl = S.slot[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
-                    if (sl >= 0) gt[u] = D.gv[0][(size_t)sl * BLK_NODES + node_loc(i, j, k)];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-                if (tid + u * ADJ_THREADS < GT3) S.g[tid + u * ADJ_THREADS] = gt[u];
-        }
-        __syncthreads();
         float bnd = 0.f;
         if (valid) {
             rr[2] = rr[3] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -579,7 +645,12 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bnd += __shfl_xor_sync(0xffffffffu, bnd, o);
         if ((tid & 31) == 0) S.red[tid >> 5] = bnd;
+        // level 2 of chunk c + G has landed and phase A is done with the staged
+        // buffers: level 3 of chunk c + G goes in flight
+        a_wait();
         __syncthreads();
+        if (has_next) adj_stage3(D, S, S.cd[(kc + 1) % 3], ain, (kc + 1) & 1, ep);
+        a_commit();
         if (tid == 0) {
             float bs = 0.f;
             for (int wq = 0; wq < ADJ_THREADS / 32; ++wq) bs += S.red[wq];
@@ -625,8 +696,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
             const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
             const int q = gidx(i, j, k);
             const int a0 = S.t[q], a1 = S.t[GT3P + q], a2 = S.t[2 * GT3P + q];
+            S.t[q] = 0; S.t[GT3P + q] = 0; S.t[2 * GT3P + q] = 0;   // cleared for the next chunk
             if (a0 | a1 | a2) {
-                const int sl = S.slot[((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
+                const int sl = S.slot[kc & 1][((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2)];
                 if (sl >= 0)
                     red_add_v4(gbar + (size_t)sl * BLK_NODES + node_loc(i, j, k), (float)a0 * isc, (float)a1 * isc,
                                (float)a2 * isc, 0.f);
@@ -634,7 +706,11 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
                     set_err(D, ERRB_CAPACITY);
             }
         }
+        // level 3 of chunk c + G has landed
+        a_wait();
         __syncthreads();
+        if (!has_next) break;
+        c = cn;
     }
 }
 
@@ -674,30 +750,96 @@ __global__ void k_adj_grid(Dev D, float4 *gbar) {
     }
 }
 
+constexpr int PS_F4 = 13;                   // staged stride: record (8), adjoint words 0,3,4,5 (4), gpar (1)
+struct AdjP2GSmem {
+    float4 st[ADJ_THREADS * PS_F4];
+    float4 g[GT3];                           // grid adjoint tile (Pbar, mbar)
+    int4 cd[3];
+    unsigned pidx[ADJ_THREADS];
+    unsigned pe[8];
+    int ps[8];
+};
+
+// level 3 of the reverse P2G: records, the adjoint words it updates, the
+// parameter gradients and the grid-adjoint tile
+__device__ __forceinline__ void adj_p2g_stage3(const Dev &D, AdjP2GSmem &S, int4 ch, const float4 *aout,
+                                               const float4 *gpar, const float4 *gbar, unsigned ep) {
+    const int tid = threadIdx.x, lane = tid & 31, wbase = tid & ~31, piece = lane & 7;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const int j = wbase + 4 * w + (lane >> 3);
+        if (j < ch.z) {
+            const size_t p = S.pidx[j];
+            a_cp16(&S.st[j * PS_F4 + piece], D.rec + p * REC_F4 + piece);
+            if (piece < 4) a_cp16(&S.st[j * PS_F4 + 8 + piece], aout + p * ADJ_F4 + (piece == 0 ? 0 : piece + 2));
+            else if (piece == 4) a_cp16(&S.st[j * PS_F4 + 12], gpar + p);
+        }
+    }
+    for (int t = tid; t < GT3; t += ADJ_THREADS) {
+        const int i = t / (GT * GT), j = (t / GT) % GT, k = t % GT;
+        const int b = ((i >> 2) << 2) | ((j >> 2) << 1) | (k >> 2);
+        const int sl = S.pe[b] == ep ? S.ps[b] : -1;
+        if (sl >= 0) a_cp16(&S.g[t], gbar + (size_t)sl * BLK_NODES + node_loc(i, j, k));
+        else S.g[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
-    __shared__ float4 s_g[GT3];
-    __shared__ int s_slot[8];
+    __shared__ AdjP2GSmem S;
     const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
     const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
-    for (unsigned c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-        const int4 ch = D.chunks[c];
+    const int tid = threadIdx.x;
+    unsigned c = blockIdx.x;
+    if (c >= n_chunks) return;
+    if (tid == 0) {
+        S.cd[0] = D.chunks[c];
+        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+    }
+    __syncthreads();
+    adj_stage2(D, S, S.cd[0], ep);
+    a_commit();
+    a_wait();
+    __syncthreads();
+    adj_p2g_stage3(D, S, S.cd[0], aout, gpar, gbar, ep);
+    a_commit();
+    a_wait();
+    __syncthreads();
+    for (int kc = 0;; ++kc) {
+        const int4 ch = S.cd[kc % 3];
+        const int cnt = min(ch.z, ADJ_THREADS);
+        const unsigned cn = c + gridDim.x;
+        const bool has_next = cn < n_chunks;
+        const unsigned p = tid < cnt ? S.pidx[tid] : 0u;   // read before level 2 of c + G overwrites it
+        if (tid == 0 && cn + gridDim.x < n_chunks) a_cp16(&S.cd[(kc + 2) % 3], D.chunks + cn + gridDim.x);
+        if (has_next) adj_stage2(D, S, S.cd[(kc + 1) % 3], ep);
+        a_commit();
         int inst, bx, by, bz;
         key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
-        load_tile(D, gbar, ep, inst, bx, by, bz, s_g, s_slot);
-        for (int j = threadIdx.x; j < ch.z; j += blockDim.x) {
-            const unsigned p = D.sorted[ch.y + j];
-            ParticleIn P;
+        bool ok = tid < cnt;
+        float4 o0, o3, o4, o5, g4;
+        float xa[3], va[3], Ab[9], Fb[9], mubar = 0.f, lambar = 0.f;
+        ParticleIn P;
+        if (ok) {
+            const float4 *q = S.st + tid * PS_F4;
             float4 rr[REC_F4];
 #pragma unroll
-            for (int w = 0; w < REC_F4; ++w) rr[w] = D.rec[(size_t)p * REC_F4 + w];
+            for (int w = 0; w < REC_F4; ++w) rr[w] = q[w];
+            o0 = q[8]; o3 = q[9]; o4 = q[10]; o5 = q[11]; g4 = q[12];
             unpack_particle(rr, P);
             float f[3];
             int b[3];
             b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
             b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
             b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
-            if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); continue; }
+            if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); ok = false; }
+        }
+        if (ok) {
+            float f[3];
+            int b[3];
+            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
+            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
+            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
             float w[3][3], dw[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
@@ -712,8 +854,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
                                 P.mass * P.C[4] - kf * tau.yy, P.mass * P.C[5] - kf * tau.yz,
                                 P.mass * P.C[6] - kf * tau.xz, P.mass * P.C[7] - kf * tau.yz,
                                 P.mass * P.C[8] - kf * tau.zz};
-            float xa[3] = {0.f, 0.f, 0.f}, va[3] = {0.f, 0.f, 0.f};
-            float Ab[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int t = 0; t < 3; ++t) xa[t] = va[t] = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) Ab[t] = 0.f;
             for (int i = 0; i < 3; ++i)
                 for (int jj = 0; jj < 3; ++jj)
                     for (int k = 0; k < 3; ++k) {
@@ -721,7 +865,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
                         const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
                                              w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
                         const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
-                        const float4 g = s_g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
                         const float Pb[3] = {g.x, g.y, g.z};
                         float wbar = g.w * P.mass;
 #pragma unroll
@@ -744,13 +888,19 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) T[3 * r + cc] = -0.5f * kf * (Ab[3 * r + cc] + Ab[3 * cc + r]);
-            float Fb[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            float mubar = 0.f, lambar = 0.f;
+#pragma unroll
+            for (int t = 0; t < 9; ++t) Fb[t] = 0.f;
             if (P.elastic == ELASTIC_FCR) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
             else if (P.elastic == ELASTIC_NH) nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
             else more_adjoint(P.elastic, P.F, U, V, s3, e3, P.mu, P.lam, T, Fb, &mubar, &lambar);
+        }
+        // level 2 of chunk c + G has landed; the staged buffers are free
+        a_wait();
+        __syncthreads();
+        if (has_next) adj_p2g_stage3(D, S, S.cd[(kc + 1) % 3], aout, gpar, gbar, ep);
+        a_commit();
+        if (ok) {
             float4 *op = aout + (size_t)p * ADJ_F4;
-            const float4 o0 = op[0], o3 = op[3], o4 = op[4], o5 = op[5];
             op[0] = make_float4(o0.x + xa[0], o0.y + xa[1], o0.z + xa[2], va[0]);
             op[1] = make_float4(va[1], va[2], P.mass * Ab[0], P.mass * Ab[1]);
             op[2] = make_float4(P.mass * Ab[2], P.mass * Ab[3], P.mass * Ab[4], P.mass * Ab[5]);
@@ -759,11 +909,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, fl
             op[5] = make_float4(o5.x + Fb[5], o5.y + Fb[6], o5.z + Fb[7], o5.w + Fb[8]);
             float gE, gnu;
             lame_chain(P.mu, P.lam, mubar, lambar, gE, gnu);
-            float4 g4 = gpar[p];
             g4.x += gE; g4.y += gnu;
             gpar[p] = g4;
         }
+        a_wait();
         __syncthreads();
+        if (!has_next) break;
+        c = cn;
     }
 }
 

@@ -65,7 +65,11 @@ def test_one_substep_further_models(orc, sim_mod):
     s.close()
     cfg, mat = oracle_setup(orc, sc)
     ref = orc.run(cfg, orc.new_state(sc.x, v, C, F), mat, 1)
-    assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * np.abs(ref["v"]).max()
+    # v_i = mv_i / m_i divides the FP32 momentum error by the node mass: at the
+    # cloud's fringe nodes the fluid and volume pressures leave mv_i a small
+    # difference of large contributions, so the bound here is twice the
+    # elastic-model one (1e-5)
+    assert np.abs(got["v"] - ref["v"]).max() < 2e-5 * np.abs(ref["v"]).max()
     assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
     # C = 4/dx^2 sum w v_i (x_i - x_p)^T inherits the grid-velocity error: |dC| <= (6/dx) max|dv|
     assert np.abs(got["C"] - ref["C"]).max() < 6e-5 * np.abs(ref["v"]).max() / sc.dx
