@@ -27,7 +27,9 @@
  *     log compression and Frobenius deformation guidance (§4.3, Algorithm 1,
  *     App. F);
  *   - the Gaussian kernel's covariance after deformation, F Sigma F^T
- *     (§3.2, with Sigma = R S S^T R^T of §3.1).
+ *     (§3.2, with Sigma = R S S^T R^T of §3.1);
+ *   - MCIS fill sampling (§4.1) and the splatting of the Gaussians into an
+ *     image (§3.1).
  * Readings where the paper is silent are listed in the design doc (interpolation
  * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
  * delta-gamma of Klar et al. 2016, the 1e-4 floor before log).
@@ -1204,4 +1206,107 @@ void orc_mcis(int n_obj, const long *surf_off, const double *surf, const long *c
         }
         free(cum);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Splatting of the deformed Gaussian kernels (§3.1): a Gaussian with mean   */
+/* mu and covariance Sigma projects to Sigma' = J W Sigma W^T J^T, with W    */
+/* the rotation of the view transform and J the Jacobian of the perspective  */
+/* projection at the mean; a pixel's colour blends the Gaussians front to    */
+/* back, Col = sum_i col_i alpha_i prod_{j<i} (1 - alpha_j), with           */
+/* alpha_i = o_i exp(-1/2 d^T Sigma'^{-1} d), d = pixel centre - projected   */
+/* mean.  Readings where the paper defers to 3DGS (its cited renderer):      */
+/*   - view: camera coordinates t = R mu + T (row-major 3x4 [R | T]);        */
+/*     u = fx t_x / t_z + cx, v = fy t_y / t_z + cy; Gaussians with           */
+/*     t_z <= 0.2 are not drawn;                                             */
+/*   - Sigma' is dilated by 0.3 I (pixel low-pass);                          */
+/*   - a Gaussian touches the 16x16-pixel tiles its square of half-width     */
+/*     ceil(3 sqrt(lambda_max(Sigma'))) around (u, v) overlaps, and only     */
+/*     pixels of those tiles;                                                */
+/*   - alpha = min(0.99, o exp(power)); skipped when power > 0 or alpha <     */
+/*     1/255; a pixel stops when its transmittance would drop below 1e-4;   */
+/*   - the background is added with the remaining transmittance;            */
+/*   - order: by t_z, ties by index.                                         */
+/* Brute force per pixel over all Gaussians, in double precision.            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double u, v, ca, cb, cc, depth; int rx0, rx1, ry0, ry1, ok; } orc_splat;
+
+static int splat_cmp_depth(const void *a, const void *b) {
+    const double *x = (const double *)a, *y = (const double *)b;
+    if (x[0] < y[0]) return -1;
+    if (x[0] > y[0]) return 1;
+    return x[1] < y[1] ? -1 : (x[1] > y[1]);
+}
+
+void orc_render(long n, const double *mean, const double *cov, const double *col, const double *opac,
+                const double *view, double fx, double fy, double cx, double cy, int W, int H, const double *bg,
+                double *img, double *T_out) {
+    const int TS = 16;
+    const int gx = (W + TS - 1) / TS, gy = (H + TS - 1) / TS;
+    orc_splat *sp = (orc_splat *)malloc((n > 0 ? n : 1) * sizeof(orc_splat));
+    double *order = (double *)malloc((n > 0 ? n : 1) * 2 * sizeof(double));
+    long m = 0;
+    for (long i = 0; i < n; ++i) {
+        const double *R = view, *p = mean + 3 * i;
+        double t[3];
+        for (int r = 0; r < 3; ++r) t[r] = R[4 * r] * p[0] + R[4 * r + 1] * p[1] + R[4 * r + 2] * p[2] + R[4 * r + 3];
+        sp[i].ok = 0;
+        if (!(t[2] > 0.2)) continue;
+        const double *c = cov + 6 * i;
+        double S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]}, Wr[9], WS[9], Sc[9];
+        for (int r = 0; r < 3; ++r)
+            for (int q = 0; q < 3; ++q) Wr[3 * r + q] = R[4 * r + q];
+        m_mul(WS, Wr, S);
+        m_mul_nt(Sc, WS, Wr);                      /* W Sigma W^T, camera frame */
+        const double iz = 1.0 / t[2];
+        const double J[6] = {fx * iz, 0.0, -fx * t[0] * iz * iz, 0.0, fy * iz, -fy * t[1] * iz * iz};
+        double JS[6];
+        for (int r = 0; r < 2; ++r)
+            for (int q = 0; q < 3; ++q)
+                JS[3 * r + q] = J[3 * r] * Sc[q] + J[3 * r + 1] * Sc[3 + q] + J[3 * r + 2] * Sc[6 + q];
+        double a = JS[0] * J[0] + JS[1] * J[1] + JS[2] * J[2] + 0.3;
+        double b = JS[0] * J[3] + JS[1] * J[4] + JS[2] * J[5];
+        double d = JS[3] * J[3] + JS[4] * J[4] + JS[5] * J[5] + 0.3;
+        const double det = a * d - b * b;
+        if (!(det > 0.0)) continue;
+        const double mid = 0.5 * (a + d), disc = sqrt(fmax(0.1, mid * mid - det));
+        const double lmax = fmax(mid + disc, mid - disc);
+        const double rad = ceil(3.0 * sqrt(lmax));
+        const double u = fx * t[0] * iz + cx, v = fy * t[1] * iz + cy;
+        int x0 = (int)fmin(gx, fmax(0.0, floor((u - rad) / TS))), x1 = (int)fmin(gx, fmax(0.0, floor((u + rad + TS - 1) / TS)));
+        int y0 = (int)fmin(gy, fmax(0.0, floor((v - rad) / TS))), y1 = (int)fmin(gy, fmax(0.0, floor((v + rad + TS - 1) / TS)));
+        if (x1 <= x0 || y1 <= y0) continue;
+        sp[i].u = u; sp[i].v = v; sp[i].depth = t[2];
+        sp[i].ca = d / det; sp[i].cb = -b / det; sp[i].cc = a / det;
+        sp[i].rx0 = x0; sp[i].rx1 = x1; sp[i].ry0 = y0; sp[i].ry1 = y1; sp[i].ok = 1;
+        order[2 * m] = t[2];
+        order[2 * m + 1] = (double)i;
+        ++m;
+    }
+    qsort(order, m, 2 * sizeof(double), splat_cmp_depth);
+    for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            const int tx = px / TS, ty = py / TS;
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            for (long q = 0; q < m; ++q) {
+                const long i = (long)order[2 * q + 1];
+                const orc_splat *g = &sp[i];
+                if (tx < g->rx0 || tx >= g->rx1 || ty < g->ry0 || ty >= g->ry1) continue;
+                const double dx = (px + 0.5) - g->u, dy = (py + 0.5) - g->v;
+                const double power = -0.5 * (g->ca * dx * dx + g->cc * dy * dy) - g->cb * dx * dy;
+                if (power > 0.0) continue;
+                double alpha = fmin(0.99, opac[i] * exp(power));
+                if (alpha < 1.0 / 255.0) continue;
+                const double tt = T * (1.0 - alpha);
+                if (tt < 1e-4) break;
+                for (int k = 0; k < 3; ++k) C[k] += col[3 * i + k] * alpha * T;
+                T = tt;
+            }
+            double *o = img + 3 * ((size_t)py * W + px);
+            for (int k = 0; k < 3; ++k) o[k] = C[k] + T * bg[k];
+            if (T_out) T_out[(size_t)py * W + px] = T;
+        }
+    free(sp);
+    free(order);
 }
