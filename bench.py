@@ -315,6 +315,7 @@ def run_ours(args):
     fb = fwd_bwd(args, dev, flush, world, dist)
     bg = bgdo_leg(args, sim, sc, (x0, v0, vol, mid), flush)
     mc = mcis_leg(args, dev, flush)
+    rd = render_leg(args, sim, sc, dev, flush)
 
     if rank == 0:
         cpu_v, cpu_t = cpu[0], cpu[1]
@@ -343,6 +344,7 @@ def run_ours(args):
             "fwd_bwd": fb,
             "bgdo": bg,
             "mcis": mc,
+            "render": rd,
         }
         print(json.dumps(line), flush=True)
     sim.close()
@@ -445,6 +447,40 @@ def mcis_leg(args, dev, flush):
             "ms": t, "candidates_per_s": nc / (t * 1e-3),
             "picked_valid": bool(((out["picked"] >= 0) & (out["picked"] < nc)).all().item()),
             "note": "CUDA events, median; includes the stream-ordered scratch allocation"}
+
+
+def render_leg(args, sim, sc, dev, flush):
+    """Splatting (§3.1) of the same scene's 300k Gaussians, deformed by a
+    stressed key frame (F Sigma F^T from the library), into a 1024 x 768
+    image; CUDA events around the whole call (projection, tile keys, radix
+    sort, compositing)."""
+    import torch
+    from paper_2602_01723_gb300 import scenes
+    from paper_2602_01723_gb300.sim import render
+    v, C, F = scenes.key_frames(sc, 1, k_seed=81, fs=0.05)[0]
+    sim.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    sim.load_covariance(scenes.gaussian_covariances(sc))
+    cov = sim.covariance()
+    col, op = scenes.gaussian_appearance(sc)
+    mean = torch.as_tensor(sc.x, device=dev)
+    col_d, op_d = torch.as_tensor(col, device=dev), torch.as_tensor(op, device=dev)
+    W, H = 1024, 768
+    view, fx, fy, cx, cy = scenes.camera(W, H)
+    render(mean, cov, col_d, op_d, view, fx, fy, cx, cy, W, H)
+    ms = []
+    for k in range(max(3, args.steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        img, T = render(mean, cov, col_d, op_d, view, fx, fy, cx, cy, W, H)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    return {"gaussians": sc.n, "width": W, "height": H, "ms": t, "gaussians_per_s": sc.n / (t * 1e-3),
+            "coverage": float((T < 0.5).float().mean().item()),
+            "note": "CUDA events, median; includes the scratch allocation and the host read of the key count"}
 
 
 def fwd_bwd(args, dev, flush, world, dist):

@@ -275,6 +275,29 @@ MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, const float 
                             double *d, double *w, int64_t *picked, void *stream);
 MPM_API const char *mpm_mcis_last_error(void);
 
+/* Splatting of Gaussian kernels into a headless image (§3.1): Gaussian i
+ * has mean mean[i] (n x 3), covariance cov[i] (n x 6: xx xy xz yy yz zz,
+ * e.g. from mpm_get_covariance), colour color[i] (n x 3) and opacity
+ * opacity[i]; it projects to Sigma' = J W Sigma W^T J^T, dilated by 0.3
+ * (pixel low-pass), and pixels composite front to back,
+ *     Col = sum_i col_i alpha_i prod_{j<i} (1 - alpha_j) + T bg,
+ *     alpha_i = min(0.99, o_i exp(-1/2 d^T Sigma'^{-1} d)).
+ * Conventions of the 3DGS renderer the paper cites: Gaussians nearer than
+ * 0.2 are not drawn; each touches the 16x16 tiles of its 3-sigma square;
+ * alpha below 1/255 is skipped; a pixel stops once its transmittance would
+ * fall below 1e-4; equal depths keep the input order.  view (host, 12
+ * floats) is the row-major 3x4 world-to-camera transform [R | T]; pixel
+ * (x, y) has centre (x + 1/2, y + 1/2) and sees u = fx t_x / t_z + cx,
+ * v = fy t_y / t_z + cy.  bg: 3 floats (host).  image (height x width x 3)
+ * and trans (height x width, nullable: final transmittance) may be host or
+ * device; the inputs too.  Synchronises the stream; the message of a failure
+ * is mpm_render_last_error(). */
+MPM_API mpm_status mpm_render(int64_t n, const float *mean, const float *cov, const float *color,
+                              const float *opacity, const float view[12], float fx, float fy, float cx, float cy,
+                              int32_t width, int32_t height, const float bg[3], float *image, float *trans,
+                              void *stream);
+MPM_API const char *mpm_render_last_error(void);
+
 /* Diagnostic: P2G of the current state into dense device arrays m
  * (n_instances * R0 * R1 * R2 floats, node (b, I, J, K) at
  * ((b * R0 + I) * R1 + J) * R2 + K) and mv (3 floats per node); the particle

@@ -73,6 +73,9 @@ SIGNATURES = {
     "mpm_mcis": (ctypes.c_int, [ctypes.c_int32, _i64p, _vp, _i64p, _vp, _i64p, _vp, ctypes.c_double, ctypes.c_double,
                                 _vp, _vp, _vp, _vp]),
     "mpm_mcis_last_error": (ctypes.c_char_p, []),
+    "mpm_render": (ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp, _vp, _f32p, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_int32, _f32p, _vp, _vp, _vp]),
+    "mpm_render_last_error": (ctypes.c_char_p, []),
     "mpm_set_tuning": (ctypes.c_int, [_ctx_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]),
     "mpm_autotune": (ctypes.c_int, [_ctx_p, ctypes.c_int32, _i32p, _vp]),
     "mpm_substep_noalloc": (ctypes.c_int, [_i32p, ctypes.c_float, ctypes.c_float, _f32p, ctypes.POINTER(mpm_material),
@@ -230,3 +233,12 @@ def mpm_mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma, eps, d, w, pick
     st = lib().mpm_mcis(n_obj, so, surf, co, cand, do, u, float(sigma), float(eps), d, w, picked, stream)
     if st != 0:
         raise MpmError(st, (lib().mpm_mcis_last_error() or b"").decode())
+
+
+def mpm_render(n, mean, cov, color, opacity, view, fx, fy, cx, cy, width, height, bg, image, trans, stream):
+    v = (ctypes.c_float * 12)(*[float(a) for a in view])
+    b = (ctypes.c_float * 3)(*[float(a) for a in bg])
+    st = lib().mpm_render(int(n), mean, cov, color, opacity, v, float(fx), float(fy), float(cx), float(cy),
+                          int(width), int(height), b, image, trans, stream)
+    if st != 0:
+        raise MpmError(st, (lib().mpm_render_last_error() or b"").decode())

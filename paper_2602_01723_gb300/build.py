@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "libmpm.so")
-SOURCES = ["mpm_api.cu", "mpm_forward.cu", "mpm_adjoint.cu", "mpm_noalloc.cu", "mpm_bgdo.cu", "mpm_gaussian.cu", "mpm_mcis.cu"]
+SOURCES = ["mpm_api.cu", "mpm_forward.cu", "mpm_adjoint.cu", "mpm_noalloc.cu", "mpm_bgdo.cu", "mpm_gaussian.cu", "mpm_mcis.cu", "mpm_render.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

@@ -451,3 +451,31 @@ def mcis_case(n_surface=(36_000, 36_000, 36_000), n_cand=(250_000, 250_000, 250_
     return {"surf_off": off(surf), "surf": _f32(np.concatenate(surf)), "cand_off": off(cand),
             "cand": _f32(np.concatenate(cand)), "draw_off": np.concatenate([[0], np.cumsum(n_draw)]).astype(np.int64),
             "u": rng.random(int(sum(n_draw)))}
+
+
+def gaussian_appearance(sc: Scene, k_seed=80, transparent=None):
+    """Per particle an RGB colour U(0, 1)^3 and an opacity U(0.3, 1) (splat
+    appearance); particles flagged in `transparent` get opacity 0, as the
+    filled interior points of §4.1 step 6."""
+    rng = _rng(k_seed)
+    col = rng.random((sc.n, 3))
+    op = rng.uniform(0.3, 1.0, sc.n)
+    if transparent is not None:
+        op[np.asarray(transparent)] = 0.0
+    return _f32(col), _f32(op)
+
+
+def camera(width, height, eye=(0.5, 0.45, -1.0), target=(0.5, 0.25, 0.5), fov_deg=40.0):
+    """A pinhole camera looking from `eye` at `target` (y up): the row-major
+    3x4 world-to-camera transform [R | T] with camera z along the view
+    direction and image y down, and fx, fy, cx, cy in pixels."""
+    e, t = np.asarray(eye, float), np.asarray(target, float)
+    z = t - e
+    z /= np.linalg.norm(z)
+    x = np.cross(np.array([0.0, -1.0, 0.0]), z)
+    x /= np.linalg.norm(x)
+    y = np.cross(z, x)
+    R = np.stack([x, y, z])
+    T = -R @ e
+    f = 0.5 * height / math.tan(math.radians(fov_deg) / 2)
+    return np.concatenate([R, T[:, None]], 1), f, f, 0.5 * width, 0.5 * height

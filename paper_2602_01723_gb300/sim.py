@@ -227,3 +227,22 @@ def mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma=0.02, eps=1e-6, devi
     L.mpm_mcis(surf_off, _p(surf), cand_off, _p(cand), draw_off, _p(u), sigma, eps, _p(out["d"]), _p(out["w"]),
                _p(out["picked"]), _stream(stream))
     return out
+
+
+def render(mean, cov, color, opacity, view, fx, fy, cx, cy, width, height, bg=(0.0, 0.0, 0.0), device="cuda",
+           stream=None):
+    """Splat the Gaussians into an image (§3.1) on the GPU.  view: 3x4
+    world-to-camera [R | T].  Returns (image (H, W, 3), transmittance (H, W))
+    as device tensors."""
+    dv = torch.device(device)
+    mean = _dev(mean, torch.float32, dv, 3)
+    n = mean.shape[0]
+    cov = _dev(cov, torch.float32, dv, 6)
+    color = _dev(color, torch.float32, dv, 3)
+    opacity = _dev(opacity, torch.float32, dv)
+    img = torch.empty((height, width, 3), device=dv)
+    tr = torch.empty((height, width), device=dv)
+    view = np.asarray(view, dtype=np.float64).reshape(-1)
+    L.mpm_render(n, _p(mean), _p(cov), _p(color), _p(opacity), view, fx, fy, cx, cy, width, height, bg, _p(img),
+                 _p(tr), _stream(stream))
+    return img, tr
