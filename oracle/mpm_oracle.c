@@ -1227,7 +1227,11 @@ void orc_mcis(int n_obj, const long *surf_off, const double *surf, const long *c
 /*     1/255; a pixel stops when its transmittance would drop below 1e-4;   */
 /*   - the background is added with the remaining transmittance;            */
 /*   - order: by t_z, ties by index.                                         */
-/* Brute force per pixel over all Gaussians, in double precision.            */
+/* Brute force per pixel over all Gaussians, in double precision, except the */
+/* depth that orders the Gaussians and decides the near-plane test: that is */
+/* a decision the kernel takes in FP32, so it is taken here in FP32 too,     */
+/* from the FP32 view and positions, one rounded operation at a time in the */
+/* kernel's order.                                                           */
 /* ------------------------------------------------------------------------ */
 
 typedef struct { double u, v, ca, cb, cc, depth; int rx0, rx1, ry0, ry1, ok; } orc_splat;
@@ -1251,8 +1255,10 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
         const double *R = view, *p = mean + 3 * i;
         double t[3];
         for (int r = 0; r < 3; ++r) t[r] = R[4 * r] * p[0] + R[4 * r + 1] * p[1] + R[4 * r + 2] * p[2] + R[4 * r + 3];
+        const float zf = (((float)R[8] * (float)p[0] + (float)R[9] * (float)p[1]) + (float)R[10] * (float)p[2]) +
+                         (float)R[11];
         sp[i].ok = 0;
-        if (!(t[2] > 0.2)) continue;
+        if (!(zf > 0.2f)) continue;
         const double *c = cov + 6 * i;
         double S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]}, Wr[9], WS[9], Sc[9];
         for (int r = 0; r < 3; ++r)
@@ -1280,7 +1286,7 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
         sp[i].u = u; sp[i].v = v; sp[i].depth = t[2];
         sp[i].ca = d / det; sp[i].cb = -b / det; sp[i].cc = a / det;
         sp[i].rx0 = x0; sp[i].rx1 = x1; sp[i].ry0 = y0; sp[i].ry1 = y1; sp[i].ok = 1;
-        order[2 * m] = t[2];
+        order[2 * m] = (double)zf;
         order[2 * m + 1] = (double)i;
         ++m;
     }

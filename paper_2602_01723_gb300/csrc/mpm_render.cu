@@ -48,7 +48,11 @@ __global__ void k_rd_pre(long long n, const float *mean, const float *cov, const
         const float px = mean[3 * i], py = mean[3 * i + 1], pz = mean[3 * i + 2];
         const float tx = c.R[0] * px + c.R[1] * py + c.R[2] * pz + c.T[0];
         const float ty = c.R[3] * px + c.R[4] * py + c.R[5] * pz + c.T[1];
-        const float tz = c.R[6] * px + c.R[7] * py + c.R[8] * pz + c.T[2];
+        // the depth orders the compositing: rounded operation by operation in a
+        // fixed order (no contraction), so that its value does not depend on
+        // the compiler
+        const float tz = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(c.R[6], px), __fmul_rn(c.R[7], py)),
+                                             __fmul_rn(c.R[8], pz)), c.T[2]);
         if (!(tz > 0.2f)) continue;
         const float *s = cov + 6 * i;
         const float S[9] = {s[0], s[1], s[2], s[1], s[3], s[4], s[2], s[4], s[5]};
