@@ -27,14 +27,17 @@ ROOT = os.path.dirname(HERE)
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 
 
+# the files the substep kernel's device code is compiled from
+KERNEL_SOURCES = ("mpm_forward.cu", "mpm_math.cuh", "mpm_dev.cuh")
+
+
 def source_hash() -> str:
-    """sha256 over the CUDA sources and headers of libmpm."""
+    """sha256 over the sources of the substep kernel's device code."""
     h = hashlib.sha256()
     csrc = os.path.join(HERE, "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, f), "rb") as fh:
-                h.update(f.encode() + b"\0" + fh.read())
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
     return h.hexdigest()[:16]
 
 
