@@ -784,7 +784,8 @@ __device__ __forceinline__ void adj_p2g_stage3(const Dev &D, AdjP2GSmem &S, int4
     }
 }
 
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
+// three CTAs per SM (168 registers, a few bytes of spill) measured faster than two at 216
+__global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
     __shared__ AdjP2GSmem S;
     const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
     const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
