@@ -315,6 +315,7 @@ def run_ours(args):
     fb = fwd_bwd(args, dev, flush, world, dist)
     bg = bgdo_leg(args, sim, sc, (x0, v0, vol, mid), flush)
     mc = mcis_leg(args, dev, flush)
+    cf = configs_leg(args, dev, flush)
     rd = render_leg(args, sim, sc, dev, flush)
 
     if rank == 0:
@@ -343,6 +344,7 @@ def run_ours(args):
             "err_vs_fp64": err,
             "fwd_bwd": fb,
             "bgdo": bg,
+            "configs": cf,
             "mcis": mc,
             "render": rd,
         }
@@ -418,6 +420,82 @@ def bgdo_leg(args, sim, sc, init, flush):
             "note": "CUDA events, medians; stage 1 includes the three snapshot copies"}
 
 
+def configs_leg(args, dev, flush):
+    """Forward throughput of the other workload shapes (the 8k cube, the
+    64-instance batch on its own 64^3 grids, the 2M-particle 256^3
+    block-sparse scene), each a full run of its substeps from the resident
+    initial state, and the batch's fwd+bwd (10-frame loss, per-instance
+    parameter gradients)."""
+    import numpy as np
+    import torch
+    from paper_2602_01723_gb300 import scenes
+    from paper_2602_01723_gb300.sim import Simulator, trajectory
+    from paper_2602_01723_gb300 import _lib as L
+    from paper_2602_01723_gb300.sim import _p, _stream
+    out = {}
+    for name in ("cube_8k", "batch_64", "large_2m"):
+        sc = scenes.WORKLOADS[name]()
+        sim = Simulator.from_scene(sc)
+        n, S = sc.n, sc.n_substeps
+        x0, v0 = torch.as_tensor(sc.x, device=dev), torch.as_tensor(sc.v, device=dev)
+        vol = torch.as_tensor(sc.vol, device=dev)
+        mid = torch.as_tensor(sc.mat_id, dtype=torch.int32, device=dev)
+        inst = None if sc.instance is None else torch.as_tensor(sc.instance, dtype=torch.int32, device=dev)
+        prm = None if sc.params is None else torch.as_tensor(sc.params, device=dev)
+        sim.n = n
+
+        def run():
+            L.mpm_load_particles(sim.ctx, n, _p(x0), _p(v0), None, None, _p(vol), _p(mid), _p(inst), _p(prm),
+                                 _stream())
+            sim.step(S)
+        run()
+        sim.sync()
+        ms = []
+        for k in range(max(2, min(args.steps, 3))):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            run()
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        out[name] = {"particles": n, "substeps": S, "ms": t, "value": n * S / (t * 1e-3), "unit": UNIT,
+                     "hbm_frac": n * S / (t * 1e-3) * FWD_BYTES_PER_PS / 1e9 / load_peaks()[0]}
+        if name == "batch_64":
+            frames = [int(f) for f in np.linspace(S / 10, S, 10)]
+            init = {"x": x0, "v": v0, "vol": vol, "mat_id": mid, "instance": inst}
+            prm0 = torch.tensor(np.stack([np.log([m["E"] for m in sc.materials]), [m["nu"] for m in sc.materials],
+                                          [m["yield_stress"] for m in sc.materials]], 1)[sc.mat_id],
+                                dtype=torch.float32, device=dev)
+            target = x0[None] + 0.005
+
+            def fb():
+                p = prm0.clone().requires_grad_(True)
+                xs = trajectory(p, sim, init, frames)
+                ((xs - target) ** 2).sum().backward()
+                return sim.reduce_by_material(p.grad)
+            fb()
+            torch.cuda.synchronize()
+            fms = []
+            for k in range(2):
+                flush.fill_(float(k))
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                g = fb()
+                e1.record()
+                torch.cuda.synchronize()
+                fms.append(e0.elapsed_time(e1))
+            tf = statistics.median(fms)
+            out[name]["fwd_bwd"] = {"ms": tf, "value": n * S / (tf * 1e-3), "unit": UNIT,
+                                    "per_instance_grads_finite": bool(torch.isfinite(g).all().item())}
+        sim.close()
+    out["note"] = "CUDA events, medians; L2 flushed between runs; inputs resident on the device"
+    return out
+
+
 def mcis_leg(args, dev, flush):
     """MCIS fill sampling (§4.1) for the three objects of the same scene:
     108k surface points, 750k candidates, 192k draws, inputs resident on the
@@ -488,6 +566,7 @@ def fwd_bwd(args, dev, flush, world, dist):
     a recorded 400-substep forward (checkpoint every 20) plus the reverse pass
     for the 10-frame position MSE against a target run with the seeded
     ground-truth parameters."""
+    import numpy as np
     import torch
     from paper_2602_01723_gb300 import scenes
     from paper_2602_01723_gb300.sim import Simulator, trajectory
