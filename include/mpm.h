@@ -96,7 +96,13 @@ typedef struct {
     int32_t threads;            /* unused (the substep kernel runs 128-thread CTAs) */
     int32_t scatter;            /* P2G scatter: 0 shared-memory float atomics, 1 int32 fixed-point
                                    shared-memory atomics (default), 2 direct global reductions */
-    int32_t reserved[7];
+    int32_t tape_grid;          /* reverse pass: 0 (default) keeps, for every state of a checkpoint
+                                   segment, the binning and grid that the segment's recompute built,
+                                   so that a reverse substep runs only its adjoint kernels (device
+                                   memory per state: about 2 KB per grid-pool block plus 12 B per
+                                   particle); 1 rebuilds them in every reverse substep.  0 falls back
+                                   to 1 when that memory cannot be allocated. */
+    int32_t reserved[6];
 } mpm_options;
 
 MPM_API mpm_status mpm_default_options(mpm_options *opt);

@@ -2,7 +2,9 @@
 // substeps) and the reverse pass of the MLS-MPM substep.
 //
 // Reverse of one substep (state S_s -> S_{s+1}), given the adjoint of S_{s+1}:
-//   recompute: bin S_s, P2G, grid update keeping (mv, m)
+//   S_s's binning and grid (mv, m and the updated v): kept in the grid tape
+//               by the segment's recompute, or rebuilt (bin S_s, P2G, grid
+//               update keeping (mv, m)) when the tape is off
 //   k_adj_g2p : reverse of the return map, the F update, advection and the
 //               G2P gathers; scatters the grid-velocity adjoint and writes the
 //               partial adjoint of x and F
@@ -969,6 +971,54 @@ __global__ void k_export_grads(int n, const float4 *gpar, const float4 *adj, flo
     }
 }
 
+// one state of a checkpoint segment as the reverse kernels read it: records,
+// binning, counters (with grid buffer `par` renamed to buffer 0) and grid
+struct TapeSlot {
+    float4 *rec;
+    unsigned *sorted;
+    int4 *chunks;
+    unsigned *ctr;
+    unsigned *active;
+    int *page;
+    unsigned *page_epoch;
+    float4 *gmv, *gv;
+};
+
+// Copies the current state, its binning and its grid (buffer par, after the
+// grid update) into a tape slot, and clears the momentum of buffer par as the
+// grid update would have.  The slot's page table receives only the entries
+// of the active blocks, tagged with this activation's epoch; entries left
+// from earlier uses carry older epochs, which the lookups reject.
+__global__ void k_tape_save(Dev D, int par, TapeSlot T) {
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    const size_t n = (size_t)D.n;
+    const unsigned n_act = min(D.ctr[CTR_N_ACTIVE + par], D.max_active);
+    const unsigned n_ch = min(D.ctr[CTR_N_CHUNKS], D.max_chunks);
+    const unsigned ep = D.ctr[CTR_EPOCH_OF + par];
+    if (tid < CTR_COUNT) {
+        unsigned v = D.ctr[tid];
+        if (tid == CTR_N_ACTIVE) v = n_act;
+        else if (tid == CTR_EPOCH_OF) v = ep;
+        else if (tid == CTR_N_CHUNKS) v = n_ch;
+        T.ctr[tid] = v;
+    }
+    for (size_t i = tid; i < n * REC_F4; i += stride) T.rec[i] = D.rec[i];
+    for (size_t i = tid; i < n; i += stride) T.sorted[i] = D.sorted[i];
+    for (size_t i = tid; i < n_ch; i += stride) T.chunks[i] = D.chunks[i];
+    for (size_t a = tid; a < n_act; a += stride) {
+        const unsigned k = D.active[par][a];
+        T.active[a] = k;
+        T.page[k] = (int)a;
+        T.page_epoch[k] = ep;
+    }
+    const size_t nodes = (size_t)n_act * BLK_NODES;
+    for (size_t i = tid; i < nodes; i += stride) {
+        T.gmv[i] = D.gmv[par][i];
+        T.gv[i] = D.gv[par][i];
+        D.gmv[par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -986,6 +1036,7 @@ void free_adjoint(AdjointStore &a) {
     if (a.frame_first) cudaFree(a.frame_first);
     if (a.frame_next) cudaFree(a.frame_next);
     if (a.seg) cudaFree(a.seg);
+    if (a.gt) cudaFree(a.gt);
     for (int e = 0; e < 2; ++e)
         if (a.seg_graph[e]) cudaGraphExecDestroy(a.seg_graph[e]);
     a = AdjointStore();
@@ -1072,15 +1123,134 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     D.rec = saved;
 }
 
+// byte offsets of the parts of one grid-tape slot (sorted index, chunks,
+// counters, active list, page table, page epochs, momentum, velocity); returns
+// the slot size
+static size_t gt_layout(const mpm_ctx *ctx, size_t off[8]) {
+    const size_t cap = (size_t)ctx->cap, pool = ctx->pool_blocks, nb = (size_t)ctx->total_blocks;
+    const size_t bytes[8] = {cap * sizeof(unsigned), (size_t)ctx->chunk_cap * sizeof(int4), CTR_COUNT * sizeof(unsigned),
+                             pool * sizeof(unsigned), nb * sizeof(int), nb * sizeof(unsigned),
+                             pool * BLK_NODES * sizeof(float4), pool * BLK_NODES * sizeof(float4)};
+    size_t o = 0;
+    for (int i = 0; i < 8; ++i) {
+        off[i] = o;
+        o += (bytes[i] + 255) & ~size_t(255);
+    }
+    return o;
+}
+
+static TapeSlot tape_slot(mpm_ctx *ctx, int j) {
+    AdjointStore &A = ctx->adj;
+    size_t off[8];
+    gt_layout(ctx, off);
+    char *b = A.gt + (size_t)j * A.gt_slot_bytes;
+    TapeSlot T;
+    T.rec = A.tape + (size_t)j * ctx->cap * REC_F4;
+    T.sorted = reinterpret_cast<unsigned *>(b + off[0]);
+    T.chunks = reinterpret_cast<int4 *>(b + off[1]);
+    T.ctr = reinterpret_cast<unsigned *>(b + off[2]);
+    T.active = reinterpret_cast<unsigned *>(b + off[3]);
+    T.page = reinterpret_cast<int *>(b + off[4]);
+    T.page_epoch = reinterpret_cast<unsigned *>(b + off[5]);
+    T.gmv = reinterpret_cast<float4 *>(b + off[6]);
+    T.gv = reinterpret_cast<float4 *>(b + off[7]);
+    return T;
+}
+
+// grid tape of `states` slots for the current capacities, zeroed (epoch 0
+// never belongs to an activation); false when it cannot be allocated
+static bool ensure_grid_tape(mpm_ctx *ctx, size_t states, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
+    const long long shape[4] = {ctx->cap, (long long)ctx->chunk_cap, (long long)ctx->pool_blocks, ctx->total_blocks};
+    if (A.gt && A.gt_states >= states && std::equal(shape, shape + 4, A.gt_shape)) return true;
+    if (A.gt) cudaFree(A.gt);
+    A.gt = nullptr;
+    A.gt_states = 0;
+    size_t off[8];
+    const size_t slot = gt_layout(ctx, off);
+    if (cudaMalloc(&A.gt, slot * states) != cudaSuccess) {
+        cudaGetLastError();
+        A.gt = nullptr;
+        return false;
+    }
+    if (cudaMemsetAsync(A.gt, 0, slot * states, st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(A.gt);
+        A.gt = nullptr;
+        return false;
+    }
+    A.gt_slot_bytes = slot;
+    A.gt_states = states;
+    std::copy(shape, shape + 4, A.gt_shape);
+    return true;
+}
+
+// The segment's forward from its checkpoint (in D.rec, binned by the
+// caller), keeping every state s = 0 .. len-1 with its binning and grid in
+// tape slot s.  The last state is scattered and its grid updated as well,
+// since its reverse substep reads them.  The grid update keeps the momentum
+// for the save, which clears it.  Leaves the last state in D.rec with no
+// binning pending.
+static void tape_segment(mpm_ctx *ctx, int len, cudaStream_t st) {
+    L_plan(ctx, 3, st);               // epochs for buffer 0 (P2G below) and 1 (first fused substep)
+    L_prepare(ctx, -1, 0, 1, st);
+    L_substep(ctx, 0, 0, 0, st);
+    for (int s = 0; s < len; ++s) {
+        const int par = s & 1;
+        const bool more = s + 1 < len;
+        L_prepare(ctx, par, more ? par ^ 1 : -1, s > 0, st, 1);
+        k_tape_save<<<ctx->grid_small, 256, 0, st>>>(ctx->D, par, tape_slot(ctx, s));
+        ++ctx->launches;
+        if (more) {
+            L_substep(ctx, 1, par, par ^ 1, st);
+            L_plan(ctx, 1 << par, st);
+        }
+    }
+}
+
+// reverse of one substep from a grid-tape slot: the adjoint kernels only
+static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *aout, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
+    Dev Dj = ctx->D;
+    Dj.rec = T.rec;
+    Dj.sorted = T.sorted;
+    Dj.chunks = T.chunks;
+    Dj.ctr = T.ctr;
+    Dj.active[0] = T.active;
+    Dj.page[0] = T.page;
+    Dj.page_epoch[0] = T.page_epoch;
+    Dj.gmv[0] = T.gmv;
+    Dj.gv[0] = T.gv;
+    const int grid = ctx->grid_sub[1];
+    k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(Dj, ain, aout, A.gpar, A.gbar);
+    k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
+    k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(Dj, aout, A.gpar, A.gbar);
+    k_adj_clear<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
+    ctx->launches += 4;
+}
+
 // One segment of the reverse pass on the checkpoint already in D.rec (whose
 // binning is the pending one): tape the segment's input states by one
 // forward pass, then reverse its substeps from the last, injecting frame
-// gradients from the device table.  Leaves the adjoint in adj[cur ^ (len & 1)].
+// gradients from the device table.  With the grid tape, the forward keeps
+// each state's binning and grid and a reverse substep runs only its adjoint
+// kernels; without it, each reverse substep rebuilds them.  Leaves the
+// adjoint in adj[cur ^ (len & 1)].
 static mpm_status segment_body(mpm_ctx *ctx, int len, int cur, int pg, cudaStream_t st) {
     Dev &D = ctx->D;
     AdjointStore &A = ctx->adj;
     const size_t n = (size_t)D.n;
     rebin(ctx, st);
+    if (A.gt && A.gt_states >= (size_t)len) {
+        tape_segment(ctx, len, st);
+        for (int j = len - 1; j >= 0; --j) {
+            k_inject_tab<<<pg, 256, 0, st>>>((int)n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j);
+            ++ctx->launches;
+            adjoint_taped(ctx, tape_slot(ctx, j), A.adj[cur], A.adj[cur ^ 1], st);
+            cur ^= 1;
+        }
+        return MPM_OK;
+    }
     if (cudaMemcpyAsync(A.tape, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
     mpm_status s;
@@ -1098,12 +1268,13 @@ static mpm_status segment_body(mpm_ctx *ctx, int len, int cur, int pg, cudaStrea
 // time a segment of this length and adjoint parity runs with these buffers
 static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, long long &launches) {
     AdjointStore &A = ctx->adj;
-    const long long key[4] = {(long long)len * 2 + cur, (long long)ctx->D.n * 1000003ll + ctx->generation,
+    const long long key[5] = {(long long)len * 2 + cur, (long long)ctx->D.n * 1000003ll + ctx->generation,
                               (long long)(uintptr_t)A.tape ^ (long long)(uintptr_t)A.gbar,
-                              (long long)(uintptr_t)A.adj[0] ^ ((long long)(uintptr_t)A.frame_first << 1)};
+                              (long long)(uintptr_t)A.adj[0] ^ ((long long)(uintptr_t)A.frame_first << 1),
+                              (long long)(uintptr_t)A.gt};
     ++A.seg_clock;
     for (int e = 0; e < 2; ++e)
-        if (A.seg_graph[e] && std::equal(key, key + 4, A.seg_key[e])) {
+        if (A.seg_graph[e] && std::equal(key, key + 5, A.seg_key[e])) {
             A.seg_used[e] = A.seg_clock;
             launches = A.seg_launches[e];
             return A.seg_graph[e];
@@ -1140,7 +1311,7 @@ static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, lon
         A.seg_graph[e] = ex;
         A.seg_launches[e] = launches;
         A.seg_used[e] = A.seg_clock;
-        std::copy(key, key + 4, A.seg_key[e]);
+        std::copy(key, key + 5, A.seg_key[e]);
     }
     return ex;
 }
@@ -1186,6 +1357,13 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         if ((s = dev_alloc(ctx, &A.tape, tape_states * (size_t)ctx->cap * REC_F4))) { A.tape_states = 0; return s; }
         A.tape_states = tape_states;
         A.tape_cap = ctx->cap;
+    }
+    if (ctx->opt.tape_grid == 0) {
+        ensure_grid_tape(ctx, tape_states, st);   // when it fails the reverse substeps rebuild the grid
+    } else if (A.gt) {
+        cudaFree(A.gt);
+        A.gt = nullptr;
+        A.gt_states = 0;
     }
     // stage dL/dx
     const size_t fbytes = (size_t)n_frames * n * 3 * sizeof(float);

@@ -349,7 +349,8 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     mpm_options o;
     mpm_default_options(&o);
     if (opt) o = *opt;
-    if (o.n_instances < 1 || o.bound < 0 || o.ckpt_every < 0 || o.scatter < 0 || o.scatter > 2 || o.chunk < 0) {
+    if (o.n_instances < 1 || o.bound < 0 || o.ckpt_every < 0 || o.scatter < 0 || o.scatter > 2 || o.chunk < 0 ||
+        o.tape_grid < 0 || o.tape_grid > 1) {
         g_create_error = "bad options";
         return MPM_ERR_INVALID_ARG;
     }

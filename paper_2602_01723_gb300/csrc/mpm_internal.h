@@ -64,10 +64,18 @@ struct AdjointStore {
     int *frame_next = nullptr;      // frames
     long long frame_cap = 0, frame_first_cap = 0;
     void *seg = nullptr;            // device SegParams
+    // grid tape: for every state of a segment, the binning, counters and grid
+    // that the recompute's forward built for it, so that a reverse substep
+    // runs only its adjoint kernels.  One allocation of gt_states slots of
+    // gt_slot_bytes (layout in tape_slot); gt_shape = particle capacity, chunk
+    // capacity, pool blocks and total blocks it was sized for.
+    char *gt = nullptr;
+    size_t gt_slot_bytes = 0, gt_states = 0;
+    long long gt_shape[4] = {0, 0, 0, 0};
     // CUDA graph of one segment's recompute + reverse, keyed by its shape
     // (a full segment and a shorter last one: two entries, least recently used replaced)
     cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
-    long long seg_key[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    long long seg_key[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
     long long seg_launches[2] = {0, 0};   // kernels one replay launches
     long long seg_used[2] = {0, 0};
     long long seg_clock = 0;

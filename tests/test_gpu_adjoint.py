@@ -74,12 +74,12 @@ def test_one_substep_adjoint_matches_oracle(orc, sim_mod, kind):
     # return map changes only the stored F; the multi-substep test covers it)
 
 
-def frame_loss_gradients(orc, sim_mod, sc, params, n_sub, frames, target, C=None, F=None):
+def frame_loss_gradients(orc, sim_mod, sc, params, n_sub, frames, target, C=None, F=None, **sim_kw):
     """The frame MSE loss L = 1/(F N) sum |x_f - target_f|^2 differentiated on
     both sides: the GPU records its forward, reads the frame positions and
     runs its reverse pass; the oracle runs its own FP64 forward with a tape
     and its own adjoint.  Returns (g_gpu, g_oracle), each (n, 3)."""
-    s = sim_mod.Simulator.from_scene(sc)
+    s = sim_mod.Simulator.from_scene(sc, **sim_kw)
     s.load(sc.x, sc.vol, sc.mat_id, v=sc.v, C=C, F=F, params=params)
     xs, prev = [], 0
     for f in frames:
@@ -99,10 +99,12 @@ def frame_loss_gradients(orc, sim_mod, sc, params, n_sub, frames, target, C=None
     return g, g_ref
 
 
-def test_multi_substep_adjoint_all_models(orc, sim_mod):
+@pytest.mark.parametrize("tape_grid", [0, 1])
+def test_multi_substep_adjoint_all_models(orc, sim_mod, tape_grid):
     """30 substeps of a mixed-material ball (FCR, NH, von Mises, Drucker-
     Prager), checkpoint every 20 (two segments), frames at 10, 20, 30; log E,
-    nu and yield-stress gradients."""
+    nu and yield-stress gradients.  tape_grid 0: the reverse substeps read the
+    binning and grid kept by the segment's recompute; 1: they rebuild them."""
     sc = scenes.ball_512()
     sc.materials = [scenes.material(0, 0, 5e3, 0.3, 100.0), scenes.material(1, 0, 5e3, 0.3, 100.0),
                     scenes.material(0, 1, 5e3, 0.3, 100.0, yield_stress=20.0),
@@ -114,7 +116,7 @@ def test_multi_substep_adjoint_all_models(orc, sim_mod):
     sc.v = (sc.v + 2.0 * rng.standard_normal((sc.n, 3))).astype(np.float32)    # shear: plastic flow
     frames = [10, 20, 30]
     target = sc.x[None].astype(np.float64) + 0.01 * rng.standard_normal((3, sc.n, 3))
-    g, g_ref = frame_loss_gradients(orc, sim_mod, sc, params, 30, frames, target)
+    g, g_ref = frame_loss_gradients(orc, sim_mod, sc, params, 30, frames, target, tape_grid=tape_grid)
     for j in range(3):
         assert np.abs(g_ref[:, j]).max() > 0
         assert rel(g[:, j], g_ref[:, j]) < GRAD_TOL, (j, rel(g[:, j], g_ref[:, j]))
