@@ -313,10 +313,10 @@ def run_ours(args):
                        "free-running positions after %d substeps" % ORACLE_SAMPLE_SUBSTEPS)
 
     fb = fwd_bwd(args, dev, flush, world, dist)
-    bg = bgdo_leg(args, sim, sc, (x0, v0, vol, mid), flush)
-    mc = mcis_leg(args, dev, flush)
-    cf = configs_leg(args, dev, flush)
-    rd = render_leg(args, sim, sc, dev, flush)
+    bg = guarded(bgdo_leg, args, sim, sc, (x0, v0, vol, mid), flush)
+    mc = guarded(mcis_leg, args, dev, flush)
+    cf = guarded(configs_leg, args, dev, flush)
+    rd = guarded(render_leg, args, sim, sc, dev, flush)
 
     if rank == 0:
         cpu_v, cpu_t = cpu[0], cpu[1]
@@ -353,6 +353,20 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def guarded(leg, *a):
+    """Runs one auxiliary leg; a failure is reported in its place (with the
+    exception) instead of losing the whole line."""
+    try:
+        return leg(*a)
+    except Exception as e:  # noqa: BLE001 -- reported, not hidden
+        import torch
+        try:
+            torch.cuda.synchronize()
+        except Exception:  # noqa: BLE001
+            pass
+        return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
 def bgdo_leg(args, sim, sc, init, flush):
@@ -424,8 +438,10 @@ def configs_leg(args, dev, flush):
     """Forward throughput of the other workload shapes (the 8k cube, the
     64-instance batch on its own 64^3 grids, the 2M-particle 256^3
     block-sparse scene), each a full run of its substeps from the resident
-    initial state, and the batch's fwd+bwd (10-frame loss, per-instance
-    parameter gradients)."""
+    initial state; fwd+bwd of the batch (10-frame loss, per-instance
+    parameter gradients) and of the 2M scene (10-frame loss, per-object
+    gradients, checkpoint every 25), with the device memory in use
+    afterwards."""
     import numpy as np
     import torch
     from paper_2602_01723_gb300 import scenes
@@ -435,6 +451,7 @@ def configs_leg(args, dev, flush):
     out = {}
     for name in ("cube_8k", "batch_64", "large_2m"):
         sc = scenes.WORKLOADS[name]()
+        free0, total = torch.cuda.mem_get_info()
         sim = Simulator.from_scene(sc)
         n, S = sc.n, sc.n_substeps
         x0, v0 = torch.as_tensor(sc.x, device=dev), torch.as_tensor(sc.v, device=dev)
@@ -463,8 +480,8 @@ def configs_leg(args, dev, flush):
         t = statistics.median(ms)
         out[name] = {"particles": n, "substeps": S, "ms": t, "value": n * S / (t * 1e-3), "unit": UNIT,
                      "hbm_frac": n * S / (t * 1e-3) * FWD_BYTES_PER_PS / 1e9 / load_peaks()[0]}
-        if name == "batch_64":
-            frames = [int(f) for f in np.linspace(S / 10, S, 10)]
+        if name in ("batch_64", "large_2m"):
+            frames = [int(f) for f in (np.linspace(S / 10, S, 10) if sc.frame_sub is None else sc.frame_sub)]
             init = {"x": x0, "v": v0, "vol": vol, "mat_id": mid, "instance": inst}
             prm0 = torch.tensor(np.stack([np.log([m["E"] for m in sc.materials]), [m["nu"] for m in sc.materials],
                                           [m["yield_stress"] for m in sc.materials]], 1)[sc.mat_id],
@@ -489,8 +506,15 @@ def configs_leg(args, dev, flush):
                 torch.cuda.synchronize()
                 fms.append(e0.elapsed_time(e1))
             tf = statistics.median(fms)
+            free1, _ = torch.cuda.mem_get_info()
             out[name]["fwd_bwd"] = {"ms": tf, "value": n * S / (tf * 1e-3), "unit": UNIT,
-                                    "per_instance_grads_finite": bool(torch.isfinite(g).all().item())}
+                                    "ckpt_every": int(sc.ckpt_every or 20), "frames": len(frames),
+                                    "grads_finite": bool(torch.isfinite(g).all().item()),
+                                    "grads": "per instance" if sc.n_instances > 1 else "per object (material id)",
+                                    "device_memory_gb": (free0 - free1) / 1e9,
+                                    "device_memory": "cudaMemGetInfo after the fwd+bwd runs minus before the context "
+                                                     "was created: the context (state, grids, checkpoints, tapes, "
+                                                     "adjoint buffers) and the run's torch tensors"}
         sim.close()
     out["note"] = "CUDA events, medians; L2 flushed between runs; inputs resident on the device"
     return out
