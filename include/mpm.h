@@ -156,7 +156,9 @@ MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream);
  * [1] occupied blocks, [2] active blocks of the last grid, [3] work chunks,
  * [4] FP64 SVD fallbacks so far, [5] substeps recorded, [6] device error
  * word, [7] grid pool capacity (blocks), [8] kernels launched by this
- * context so far; [9..15] zero. */
+ * context so far, [9] grid-tape pool blocks per recorded state (0: no grid
+ * tape), [10] reverse passes run again because a state's grid did not fit
+ * its grid-tape slot; [11..15] zero. */
 MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream);
 
 /* Tracing of the substep kernel.  When ms and count are not NULL, first

@@ -988,13 +988,20 @@ struct TapeSlot {
 // grid update) into a tape slot, and clears the momentum of buffer par as the
 // grid update would have.  The slot's page table receives only the entries
 // of the active blocks, tagged with this activation's epoch; entries left
-// from earlier uses carry older epochs, which the lookups reject.
-__global__ void k_tape_save(Dev D, int par, TapeSlot T) {
+// from earlier uses carry older epochs, which the lookups reject.  A grid of
+// more than gcap active blocks does not fit the slot: the kernel raises
+// *over and records an empty slot (no chunks, no blocks), whose reverse
+// kernels then do nothing; the host re-runs the reverse pass with larger
+// slots.
+__global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned *over) {
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     const size_t n = (size_t)D.n;
-    const unsigned n_act = min(D.ctr[CTR_N_ACTIVE + par], D.max_active);
-    const unsigned n_ch = min(D.ctr[CTR_N_CHUNKS], D.max_chunks);
+    const unsigned n_all = min(D.ctr[CTR_N_ACTIVE + par], D.max_active);
+    const bool fits = n_all <= gcap;
+    const unsigned n_act = fits ? n_all : 0u;
+    const unsigned n_ch = fits ? min(D.ctr[CTR_N_CHUNKS], D.max_chunks) : 0u;
     const unsigned ep = D.ctr[CTR_EPOCH_OF + par];
+    if (tid == 0 && !fits) atomicOr(over, 1u);
     if (tid < CTR_COUNT) {
         unsigned v = D.ctr[tid];
         if (tid == CTR_N_ACTIVE) v = n_act;
@@ -1011,10 +1018,12 @@ __global__ void k_tape_save(Dev D, int par, TapeSlot T) {
         T.page[k] = (int)a;
         T.page_epoch[k] = ep;
     }
-    const size_t nodes = (size_t)n_act * BLK_NODES;
+    const size_t kept = (size_t)n_act * BLK_NODES, nodes = (size_t)n_all * BLK_NODES;
     for (size_t i = tid; i < nodes; i += stride) {
-        T.gmv[i] = D.gmv[par][i];
-        T.gv[i] = D.gv[par][i];
+        if (i < kept) {
+            T.gmv[i] = D.gmv[par][i];
+            T.gv[i] = D.gv[par][i];
+        }
         D.gmv[par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
@@ -1037,7 +1046,10 @@ void free_adjoint(AdjointStore &a) {
     if (a.frame_next) cudaFree(a.frame_next);
     if (a.seg) cudaFree(a.seg);
     if (a.gt) cudaFree(a.gt);
-    for (int e = 0; e < 2; ++e)
+    if (a.side) cudaStreamDestroy(a.side);
+    if (a.ev_fork) cudaEventDestroy(a.ev_fork);
+    if (a.ev_join) cudaEventDestroy(a.ev_join);
+    for (int e = 0; e < AdjointStore::NGRAPH; ++e)
         if (a.seg_graph[e]) cudaGraphExecDestroy(a.seg_graph[e]);
     a = AdjointStore();
 }
@@ -1123,75 +1135,115 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     D.rec = saved;
 }
 
-// byte offsets of the parts of one grid-tape slot (sorted index, chunks,
-// counters, active list, page table, page epochs, momentum, velocity); returns
-// the slot size
-static size_t gt_layout(const mpm_ctx *ctx, size_t off[8]) {
-    const size_t cap = (size_t)ctx->cap, pool = ctx->pool_blocks, nb = (size_t)ctx->total_blocks;
-    const size_t bytes[8] = {cap * sizeof(unsigned), (size_t)ctx->chunk_cap * sizeof(int4), CTR_COUNT * sizeof(unsigned),
-                             pool * sizeof(unsigned), nb * sizeof(int), nb * sizeof(unsigned),
-                             pool * BLK_NODES * sizeof(float4), pool * BLK_NODES * sizeof(float4)};
+constexpr size_t GT_HEADER = 256;   // grid-tape header: word 0 = overflow flag
+
+// byte offsets of the parts of one grid-tape slot (records, sorted index,
+// chunks, counters, active list, page table, page epochs, momentum, velocity)
+// for a grid pool of `pool` blocks; returns the slot size
+static size_t gt_layout(const mpm_ctx *ctx, unsigned pool, size_t off[9]) {
+    const size_t cap = (size_t)ctx->cap, nb = (size_t)ctx->total_blocks, gp = pool;
+    const size_t bytes[9] = {cap * REC_F4 * sizeof(float4), cap * sizeof(unsigned), (size_t)ctx->chunk_cap * sizeof(int4),
+                             CTR_COUNT * sizeof(unsigned), gp * sizeof(unsigned), nb * sizeof(int), nb * sizeof(unsigned),
+                             gp * BLK_NODES * sizeof(float4), gp * BLK_NODES * sizeof(float4)};
     size_t o = 0;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 9; ++i) {
         off[i] = o;
         o += (bytes[i] + 255) & ~size_t(255);
     }
     return o;
 }
 
-static TapeSlot tape_slot(mpm_ctx *ctx, int j) {
+static TapeSlot tape_slot(mpm_ctx *ctx, int bank, int j) {
     AdjointStore &A = ctx->adj;
-    size_t off[8];
-    gt_layout(ctx, off);
-    char *b = A.gt + (size_t)j * A.gt_slot_bytes;
+    size_t off[9];
+    gt_layout(ctx, A.gt_pool, off);
+    char *b = A.gt + GT_HEADER + ((size_t)bank * A.gt_bank_states + (size_t)j) * A.gt_slot_bytes;
     TapeSlot T;
-    T.rec = A.tape + (size_t)j * ctx->cap * REC_F4;
-    T.sorted = reinterpret_cast<unsigned *>(b + off[0]);
-    T.chunks = reinterpret_cast<int4 *>(b + off[1]);
-    T.ctr = reinterpret_cast<unsigned *>(b + off[2]);
-    T.active = reinterpret_cast<unsigned *>(b + off[3]);
-    T.page = reinterpret_cast<int *>(b + off[4]);
-    T.page_epoch = reinterpret_cast<unsigned *>(b + off[5]);
-    T.gmv = reinterpret_cast<float4 *>(b + off[6]);
-    T.gv = reinterpret_cast<float4 *>(b + off[7]);
+    T.rec = reinterpret_cast<float4 *>(b + off[0]);
+    T.sorted = reinterpret_cast<unsigned *>(b + off[1]);
+    T.chunks = reinterpret_cast<int4 *>(b + off[2]);
+    T.ctr = reinterpret_cast<unsigned *>(b + off[3]);
+    T.active = reinterpret_cast<unsigned *>(b + off[4]);
+    T.page = reinterpret_cast<int *>(b + off[5]);
+    T.page_epoch = reinterpret_cast<unsigned *>(b + off[6]);
+    T.gmv = reinterpret_cast<float4 *>(b + off[7]);
+    T.gv = reinterpret_cast<float4 *>(b + off[8]);
     return T;
 }
 
-// grid tape of `states` slots for the current capacities, zeroed (epoch 0
-// never belongs to an activation); false when it cannot be allocated
+static unsigned *gt_over(mpm_ctx *ctx) { return reinterpret_cast<unsigned *>(ctx->adj.gt); }
+
+// grid-pool blocks per slot: the whole pool after an overflow, else twice
+// the larger activation of the two working grids plus slack (the recorded
+// end state's; read synchronously, once per allocation)
+static unsigned gt_pool_for(mpm_ctx *ctx, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
+    if (A.gt_pool_want) return std::min(A.gt_pool_want, ctx->pool_blocks);
+    unsigned c[CTR_COUNT];
+    if (cudaMemcpyAsync(c, ctx->D.ctr, sizeof(c), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx->pool_blocks;
+    }
+    const unsigned long long want = 2ull * std::max(c[CTR_N_ACTIVE], c[CTR_N_ACTIVE + 1]) + 256ull;
+    return (unsigned)std::min<unsigned long long>(want, ctx->pool_blocks);
+}
+
+// the side stream and fork / join events of the overlapped reverse pass
+static bool ensure_side(mpm_ctx *ctx) {
+    AdjointStore &A = ctx->adj;
+    if (!A.side && cudaStreamCreateWithFlags(&A.side, cudaStreamNonBlocking) != cudaSuccess) A.side = nullptr;
+    if (!A.ev_fork && cudaEventCreateWithFlags(&A.ev_fork, cudaEventDisableTiming) != cudaSuccess) A.ev_fork = nullptr;
+    if (!A.ev_join && cudaEventCreateWithFlags(&A.ev_join, cudaEventDisableTiming) != cudaSuccess) A.ev_join = nullptr;
+    if (A.side && A.ev_fork && A.ev_join) return true;
+    cudaGetLastError();
+    return false;
+}
+
+// grid tape of two banks of `states` slots for the current capacities,
+// zeroed (epoch 0 never belongs to an activation, and the overflow flag
+// starts clear); false when it cannot be allocated
 static bool ensure_grid_tape(mpm_ctx *ctx, size_t states, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
-    const long long shape[4] = {ctx->cap, (long long)ctx->chunk_cap, (long long)ctx->pool_blocks, ctx->total_blocks};
-    if (A.gt && A.gt_states >= states && std::equal(shape, shape + 4, A.gt_shape)) return true;
+    const long long shape[3] = {ctx->cap, (long long)ctx->chunk_cap, ctx->total_blocks};
+    if (A.gt && A.gt_bank_states >= states && std::equal(shape, shape + 3, A.gt_shape) &&
+        (!A.gt_pool_want || A.gt_pool >= std::min(A.gt_pool_want, ctx->pool_blocks)))
+        return true;
     if (A.gt) cudaFree(A.gt);
     A.gt = nullptr;
-    A.gt_states = 0;
-    size_t off[8];
-    const size_t slot = gt_layout(ctx, off);
-    if (cudaMalloc(&A.gt, slot * states) != cudaSuccess) {
+    A.gt_bank_states = 0;
+    if (!ensure_side(ctx)) return false;
+    const unsigned pool = gt_pool_for(ctx, st);
+    size_t off[9];
+    const size_t slot = gt_layout(ctx, pool, off), bytes = GT_HEADER + 2 * states * slot;
+    if (cudaMalloc(&A.gt, bytes) != cudaSuccess) {
         cudaGetLastError();
         A.gt = nullptr;
         return false;
     }
-    if (cudaMemsetAsync(A.gt, 0, slot * states, st) != cudaSuccess) {
+    if (cudaMemsetAsync(A.gt, 0, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         cudaFree(A.gt);
         A.gt = nullptr;
         return false;
     }
     A.gt_slot_bytes = slot;
-    A.gt_states = states;
-    std::copy(shape, shape + 4, A.gt_shape);
+    A.gt_bank_states = states;
+    A.gt_pool = pool;
+    std::copy(shape, shape + 3, A.gt_shape);
+    A.gt_shape[3] = pool;
+    ++A.gt_gen;
     return true;
 }
 
 // The segment's forward from its checkpoint (in D.rec, binned by the
 // caller), keeping every state s = 0 .. len-1 with its binning and grid in
-// tape slot s.  The last state is scattered and its grid updated as well,
-// since its reverse substep reads them.  The grid update keeps the momentum
-// for the save, which clears it.  Leaves the last state in D.rec with no
-// binning pending.
-static void tape_segment(mpm_ctx *ctx, int len, cudaStream_t st) {
+// slot s of grid-tape bank `bank`.  The last state is scattered and its grid
+// updated as well, since its reverse substep reads them.  The grid update
+// keeps the momentum for the save, which clears it.  Leaves the last state
+// in D.rec with no binning pending.
+static void tape_segment(mpm_ctx *ctx, int len, int bank, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
     L_plan(ctx, 3, st);               // epochs for buffer 0 (P2G below) and 1 (first fused substep)
     L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
@@ -1199,7 +1251,7 @@ static void tape_segment(mpm_ctx *ctx, int len, cudaStream_t st) {
         const int par = s & 1;
         const bool more = s + 1 < len;
         L_prepare(ctx, par, more ? par ^ 1 : -1, s > 0, st, 1);
-        k_tape_save<<<ctx->grid_small, 256, 0, st>>>(ctx->D, par, tape_slot(ctx, s));
+        k_tape_save<<<ctx->grid_small, 256, 0, st>>>(ctx->D, par, tape_slot(ctx, bank, s), A.gt_pool, gt_over(ctx));
         ++ctx->launches;
         if (more) {
             L_substep(ctx, 1, par, par ^ 1, st);
@@ -1229,28 +1281,28 @@ static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *
     ctx->launches += 4;
 }
 
-// One segment of the reverse pass on the checkpoint already in D.rec (whose
-// binning is the pending one): tape the segment's input states by one
-// forward pass, then reverse its substeps from the last, injecting frame
-// gradients from the device table.  With the grid tape, the forward keeps
-// each state's binning and grid and a reverse substep runs only its adjoint
-// kernels; without it, each reverse substep rebuilds them.  Leaves the
-// adjoint in adj[cur ^ (len & 1)].
+// reverse substeps len-1 .. 0 of a segment from grid-tape bank `bank`,
+// injecting the frame gradients from the device table
+static void reverse_segment(mpm_ctx *ctx, int len, int bank, int cur, int pg, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
+    const int n = ctx->D.n;
+    for (int j = len - 1; j >= 0; --j) {
+        k_inject_tab<<<pg, 256, 0, st>>>(n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j);
+        ++ctx->launches;
+        adjoint_taped(ctx, tape_slot(ctx, bank, j), A.adj[cur], A.adj[cur ^ 1], st);
+        cur ^= 1;
+    }
+}
+
+// One segment of the reverse pass without the grid tape, on the checkpoint
+// already in D.rec: tape the segment's states by one forward pass, then
+// reverse its substeps from the last, each rebuilding its state's binning
+// and grid.  Leaves the adjoint in adj[cur ^ (len & 1)].
 static mpm_status segment_body(mpm_ctx *ctx, int len, int cur, int pg, cudaStream_t st) {
     Dev &D = ctx->D;
     AdjointStore &A = ctx->adj;
     const size_t n = (size_t)D.n;
     rebin(ctx, st);
-    if (A.gt && A.gt_states >= (size_t)len) {
-        tape_segment(ctx, len, st);
-        for (int j = len - 1; j >= 0; --j) {
-            k_inject_tab<<<pg, 256, 0, st>>>((int)n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j);
-            ++ctx->launches;
-            adjoint_taped(ctx, tape_slot(ctx, j), A.adj[cur], A.adj[cur ^ 1], st);
-            cur ^= 1;
-        }
-        return MPM_OK;
-    }
     if (cudaMemcpyAsync(A.tape, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return ctx_fail(ctx, MPM_ERR_CUDA, "tape copy");
     mpm_status s;
@@ -1264,22 +1316,58 @@ static mpm_status segment_body(mpm_ctx *ctx, int len, int cur, int pg, cudaStrea
     return MPM_OK;
 }
 
-// the segment as a CUDA graph, captured on the library's own stream the first
-// time a segment of this length and adjoint parity runs with these buffers
-static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, long long &launches) {
+// One step of the reverse pass.  kind 0: a whole segment without the grid
+// tape (lenR substeps, adjoint parity cur).  kind 1: the reverse of a
+// segment of lenR substeps (0: none) from grid-tape bank bankR and, at the
+// same time on the side stream, the recompute of the segment before it
+// (lenP substeps, 0: none) into bank bankP, from the checkpoint the caller
+// has put in D.rec.  The two touch disjoint memory: the recompute the
+// working state, grids and binning, the reverse only its bank's slots and
+// the adjoint buffers.
+struct RevJob {
+    int kind, lenR, bankR, cur, lenP, bankP;
+};
+
+static mpm_status run_job(mpm_ctx *ctx, const RevJob &J, int pg, cudaStream_t st) {
+    if (J.kind == 0) return segment_body(ctx, J.lenR, J.cur, pg, st);
     AdjointStore &A = ctx->adj;
-    const long long key[5] = {(long long)len * 2 + cur, (long long)ctx->D.n * 1000003ll + ctx->generation,
-                              (long long)(uintptr_t)A.tape ^ (long long)(uintptr_t)A.gbar,
-                              (long long)(uintptr_t)A.adj[0] ^ ((long long)(uintptr_t)A.frame_first << 1),
-                              (long long)(uintptr_t)A.gt};
+    const bool fork = J.lenP > 0 && J.lenR > 0;
+    cudaStream_t sp = st;
+    if (fork) {
+        if (cudaEventRecord(A.ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(A.side, A.ev_fork, 0) != cudaSuccess)
+            return ctx_fail(ctx, MPM_ERR_CUDA, "reverse pass: stream fork");
+        sp = A.side;
+    }
+    if (J.lenP > 0) {
+        rebin(ctx, sp);
+        tape_segment(ctx, J.lenP, J.bankP, sp);
+    }
+    if (J.lenR > 0) reverse_segment(ctx, J.lenR, J.bankR, J.cur, pg, st);
+    if (fork && (cudaEventRecord(A.ev_join, A.side) != cudaSuccess || cudaStreamWaitEvent(st, A.ev_join, 0) != cudaSuccess))
+        return ctx_fail(ctx, MPM_ERR_CUDA, "reverse pass: stream join");
+    return MPM_OK;
+}
+
+// the step as a CUDA graph, captured on the library's own stream (the side
+// stream joins the capture through the fork event) the first time a step of
+// this shape runs with these buffers
+static cudaGraphExec_t job_graph(mpm_ctx *ctx, const RevJob &J, int pg, long long &launches) {
+    AdjointStore &A = ctx->adj;
+    constexpr int NK = AdjointStore::NKEY, NG = AdjointStore::NGRAPH;
+    auto u = [](const void *p) { return (long long)(uintptr_t)p; };
+    const long long key[NK] = {J.kind, J.lenR, J.bankR * 2 + J.cur, J.lenP * 2 + J.bankP,
+                               (long long)ctx->D.n * 1000003ll + ctx->generation, u(A.gbar), u(A.adj[0]), u(A.adj[1]),
+                               u(A.gpar), u(A.frame_first), u(A.frame_next), u(A.seg), u(A.tape), A.gt_gen};
     ++A.seg_clock;
-    for (int e = 0; e < 2; ++e)
-        if (A.seg_graph[e] && std::equal(key, key + 5, A.seg_key[e])) {
+    for (int e = 0; e < NG; ++e)
+        if (A.seg_graph[e] && std::equal(key, key + NK, A.seg_key[e])) {
             A.seg_used[e] = A.seg_clock;
             launches = A.seg_launches[e];
             return A.seg_graph[e];
         }
-    const int e = A.seg_used[0] <= A.seg_used[1] ? 0 : 1;   // least recently used entry
+    int e = 0;   // least recently used entry
+    for (int i = 1; i < NG; ++i)
+        if (A.seg_used[i] < A.seg_used[e]) e = i;
     if (A.seg_graph[e]) { cudaGraphExecDestroy(A.seg_graph[e]); A.seg_graph[e] = nullptr; }
     if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
@@ -1293,7 +1381,7 @@ static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, lon
         cudaGetLastError();
         return nullptr;
     }
-    const mpm_status s = segment_body(ctx, len, cur, pg, ctx->cap_stream);
+    const mpm_status s = run_job(ctx, J, pg, ctx->cap_stream);
     if (cudaStreamEndCapture(ctx->cap_stream, &g) != cudaSuccess || !g || s) {
         cudaGetLastError();
         if (g) cudaGraphDestroy(g);
@@ -1311,9 +1399,23 @@ static cudaGraphExec_t segment_graph(mpm_ctx *ctx, int len, int cur, int pg, lon
         A.seg_graph[e] = ex;
         A.seg_launches[e] = launches;
         A.seg_used[e] = A.seg_clock;
-        std::copy(key, key + 5, A.seg_key[e]);
+        std::copy(key, key + NK, A.seg_key[e]);
     }
     return ex;
+}
+
+// runs one step: its graph where graphs are in use, else directly
+static mpm_status run_step(mpm_ctx *ctx, const RevJob &J, int pg, cudaStream_t st) {
+    long long per = 0;
+    cudaGraphExec_t ex = (ctx->use_graph && !ctx->trace_on) ? job_graph(ctx, J, pg, per) : nullptr;
+    if (!ex) return run_job(ctx, J, pg, st);
+    if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+        cudaGetLastError();
+        return ctx_fail(ctx, MPM_ERR_CUDA, "reverse-pass graph launch failed");
+    }
+    ctx->launches += per;
+    ctx->bins_pending = false;    // every step ends with its binning consumed
+    return MPM_OK;
 }
 
 }  // namespace mpm
@@ -1353,17 +1455,26 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
             return ctx_fail(ctx, MPM_ERR_CUDA, "memset");
     }
     const size_t tape_states = (size_t)std::min<long long>(k, S);
-    if (A.tape_states < tape_states || A.tape_cap != ctx->cap) {
-        if ((s = dev_alloc(ctx, &A.tape, tape_states * (size_t)ctx->cap * REC_F4))) { A.tape_states = 0; return s; }
-        A.tape_states = tape_states;
-        A.tape_cap = ctx->cap;
-    }
-    if (ctx->opt.tape_grid == 0) {
-        ensure_grid_tape(ctx, tape_states, st);   // when it fails the reverse substeps rebuild the grid
-    } else if (A.gt) {
+    bool use_gt = ctx->opt.tape_grid == 0 && ensure_grid_tape(ctx, tape_states, st);
+    if (ctx->opt.tape_grid != 0 && A.gt) {
         cudaFree(A.gt);
         A.gt = nullptr;
-        A.gt_states = 0;
+        A.gt_bank_states = 0;
+    }
+    auto ensure_record_tape = [&]() -> mpm_status {
+        if (A.tape_states >= tape_states && A.tape_cap == ctx->cap) return MPM_OK;
+        mpm_status r = dev_alloc(ctx, &A.tape, tape_states * (size_t)ctx->cap * REC_F4);
+        if (r) { A.tape_states = 0; return r; }
+        A.tape_states = tape_states;
+        A.tape_cap = ctx->cap;
+        return MPM_OK;
+    };
+    if (use_gt) {
+        if (A.tape) cudaFree(A.tape);   // the grid tape holds the records too
+        A.tape = nullptr;
+        A.tape_states = 0;
+    } else if ((s = ensure_record_tape())) {
+        return s;
     }
     // stage dL/dx
     const size_t fbytes = (size_t)n_frames * n * 3 * sizeof(float);
@@ -1377,9 +1488,7 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
             return ctx_fail(ctx, MPM_ERR_CUDA, "dL_dx copy");
         dldx = A.frames;
     }
-    if (cudaMemcpyAsync(A.final_state, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(A.adj[0], 0, n * ADJ_F4 * sizeof(float4), st) != cudaSuccess ||
-        cudaMemsetAsync(A.gpar, 0, n * sizeof(float4), st) != cudaSuccess)
+    if (cudaMemcpyAsync(A.final_state, D.rec, n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
     // frame table: per substep the first frame taken after it, per frame the next one there
     if (A.frame_first_cap < S + 1) {
@@ -1408,32 +1517,44 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
             cudaMemcpyAsync(A.frame_next, next.data(), next.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
             return ctx_fail(ctx, MPM_ERR_CUDA, "frame table copy");
     }
-    int cur = 0;
     const int pg = grid_for((long long)n, 256);
     const long long nseg = (S + k - 1) / k;
-    for (long long c = nseg - 1; c >= 0; --c) {
-        const long long s0 = c * k;
-        const int len = (int)std::min<long long>(k, S - s0);
-        // the segment's input state, its pending binning consumed here so that
-        // every segment starts from the same host-side state
-        if (cudaMemcpyAsync(D.rec, A.ckpt[(size_t)c], n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-            return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
+    auto seg_len = [&](long long c) { return (int)std::min<long long>(k, S - c * k); };
+    auto restore = [&](long long c) -> bool {
+        return cudaMemcpyAsync(D.rec, A.ckpt[(size_t)c], n * REC_F4 * sizeof(float4), cudaMemcpyDeviceToDevice, st) ==
+               cudaSuccess;
+    };
+    for (int attempt = 0;; ++attempt) {
+    if (cudaMemsetAsync(A.adj[0], 0, n * ADJ_F4 * sizeof(float4), st) != cudaSuccess ||
+        cudaMemsetAsync(A.gpar, 0, n * sizeof(float4), st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
+    int cur = 0;
+    if (use_gt) {
+        // the last segment's recompute, then per segment c its reverse
+        // alongside the recompute of segment c-1 (banks alternate by parity)
+        if (!restore(nseg - 1)) return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
         if (ctx->bins_pending) L_plan(ctx, 0, st);
-        k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, s0);
-        ++ctx->launches;
-        long long per = 0;
-        cudaGraphExec_t ex = (ctx->use_graph && !ctx->trace_on) ? segment_graph(ctx, len, cur, pg, per) : nullptr;
-        if (ex) {
-            if (cudaGraphLaunch(ex, st) != cudaSuccess) {
-                cudaGetLastError();
-                return ctx_fail(ctx, MPM_ERR_CUDA, "segment graph launch failed");
-            }
-            ctx->launches += per;
-            ctx->bins_pending = false;    // the segment ends with its plan consumed
-        } else if ((s = segment_body(ctx, len, cur, pg, st))) {
-            return s;
+        if ((s = run_step(ctx, RevJob{1, 0, 0, 0, seg_len(nseg - 1), (int)((nseg - 1) & 1)}, pg, st))) return s;
+        for (long long c = nseg - 1; c >= 0; --c) {
+            if (c > 0 && !restore(c - 1)) return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
+            k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, c * k);
+            ++ctx->launches;
+            const RevJob J{1, seg_len(c), (int)(c & 1), cur, c > 0 ? seg_len(c - 1) : 0,
+                           c > 0 ? (int)((c - 1) & 1) : 0};
+            if ((s = run_step(ctx, J, pg, st))) return s;
+            cur ^= (seg_len(c) & 1);
         }
-        cur ^= (len & 1);
+    } else {
+        for (long long c = nseg - 1; c >= 0; --c) {
+            // the segment's input state, its pending binning consumed here so
+            // that every segment starts from the same host-side state
+            if (!restore(c)) return ctx_fail(ctx, MPM_ERR_CUDA, "checkpoint restore");
+            if (ctx->bins_pending) L_plan(ctx, 0, st);
+            k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, c * k);
+            ++ctx->launches;
+            if ((s = run_step(ctx, RevJob{0, seg_len(c), 0, cur, 0, 0}, pg, st))) return s;
+            cur ^= (seg_len(c) & 1);
+        }
     }
     // frames taken at substep 0
     k_set_seg<<<1, 1, 0, st>>>((SegParams *)A.seg, dldx, -1);
@@ -1461,5 +1582,18 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         return ctx_fail(ctx, MPM_ERR_CUDA, "state restore");
     rebin(ctx, st);
     if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, MPM_ERR_CUDA, "reverse-pass launch failed");
-    return ctx_check(ctx, st);
+    if ((s = ctx_check(ctx, st))) return s;
+    if (!use_gt) return MPM_OK;
+    unsigned over = 0;
+    if (cudaMemcpy(&over, gt_over(ctx), sizeof(over), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "grid-tape flag read");
+    if (!over) return MPM_OK;
+    if (attempt > 0) return ctx_fail(ctx, MPM_ERR_CAPACITY, "grid tape overflow with the whole pool per slot");
+    // a state's grid did not fit its slot: slots of the whole pool (or, if
+    // those do not fit, no grid tape), and the reverse pass again
+    A.gt_pool_want = ctx->pool_blocks;
+    ++A.gt_reruns;
+    use_gt = ensure_grid_tape(ctx, tape_states, st);
+    if (!use_gt && (s = ensure_record_tape())) return s;
+    }
 }

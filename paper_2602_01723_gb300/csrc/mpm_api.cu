@@ -557,6 +557,8 @@ MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream) {
     counters[6] = err;
     counters[7] = ctx->pool_blocks;
     counters[8] = ctx->launches;
+    counters[9] = ctx->adj.gt ? ctx->adj.gt_pool : 0;
+    counters[10] = ctx->adj.gt_reruns;
     return MPM_OK;
 }
 

@@ -64,20 +64,31 @@ struct AdjointStore {
     int *frame_next = nullptr;      // frames
     long long frame_cap = 0, frame_first_cap = 0;
     void *seg = nullptr;            // device SegParams
-    // grid tape: for every state of a segment, the binning, counters and grid
-    // that the recompute's forward built for it, so that a reverse substep
-    // runs only its adjoint kernels.  One allocation of gt_states slots of
-    // gt_slot_bytes (layout in tape_slot); gt_shape = particle capacity, chunk
-    // capacity, pool blocks and total blocks it was sized for.
+    // grid tape: for every state of a segment its records, binning, counters
+    // and grid, kept from the segment's recompute so that a reverse substep
+    // runs only its adjoint kernels.  Two banks, so that the recompute of the
+    // next segment (on `side`) overlaps the reverse of the current one.  One
+    // allocation: a 256-byte header (word 0: grid-pool overflow flag), then
+    // bank 0's gt_bank_states slots, then bank 1's, gt_slot_bytes each (layout
+    // in gt_layout).  gt_pool: grid-pool blocks per slot; gt_shape: particle
+    // capacity, chunk capacity, total blocks and gt_pool it was sized for.
     char *gt = nullptr;
-    size_t gt_slot_bytes = 0, gt_states = 0;
+    size_t gt_slot_bytes = 0, gt_bank_states = 0;
+    unsigned gt_pool = 0;
+    unsigned gt_pool_want = 0;      // grid-pool blocks per slot after an overflow
     long long gt_shape[4] = {0, 0, 0, 0};
-    // CUDA graph of one segment's recompute + reverse, keyed by its shape
-    // (a full segment and a shorter last one: two entries, least recently used replaced)
-    cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
-    long long seg_key[2][5] = {{-1, -1, -1, -1, -1}, {-1, -1, -1, -1, -1}};
-    long long seg_launches[2] = {0, 0};   // kernels one replay launches
-    long long seg_used[2] = {0, 0};
+    long long gt_gen = 0;           // counts grid-tape allocations (part of the graph keys)
+    long long gt_reruns = 0;        // reverse passes run again after a grid-tape overflow
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // CUDA graphs of the reverse pass's steps, keyed by their shape (segment
+    // lengths, banks, adjoint parity) and buffers; least recently used replaced
+    static constexpr int NGRAPH = 6;
+    static constexpr int NKEY = 14;
+    cudaGraphExec_t seg_graph[NGRAPH] = {};
+    long long seg_key[NGRAPH][NKEY] = {};
+    long long seg_launches[NGRAPH] = {};
+    long long seg_used[NGRAPH] = {};
     long long seg_clock = 0;
 };
 void free_adjoint(AdjointStore &a);

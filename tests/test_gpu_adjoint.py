@@ -200,3 +200,56 @@ def test_backward_argument_errors(sim_mod):
     with pytest.raises(L.MpmError):
         s.step(1, record=True)
     s.close()
+
+
+def test_grid_tape_overflow_reruns_with_whole_pool_slots(orc, sim_mod):
+    """The grid tape sizes each recorded state's grid slot from the active
+    blocks seen when it is allocated.  A context first differentiates a
+    compact 512-particle ball on a 64^3 grid (small slots), then the same
+    number of particles spread over [0.15, 0.85]^3 (about twenty times the
+    active blocks): its states overflow their slots, the reverse pass runs
+    again with slots of the whole pool, and the gradients of the spread
+    scene match the FP64 oracle.  30 substeps, checkpoint every 10 (the
+    overlapped segment steps run), frames at 10, 20, 30, stressed start."""
+    R, dx, dt, n = 64, 1.0 / 64, 1e-4, 512
+    mats = [scenes.material(0, 0, 5e3, 0.3, 100.0)]
+    rng = np.random.default_rng(11)
+    xa, h = scenes._jittered_ball(n, (0.5, 0.3, 0.5), 0.05, rng)
+    xb = rng.uniform(0.15, 0.85, (n, 3)).astype(np.float32)
+    F = (np.eye(3)[None] + 0.02 * rng.standard_normal((n, 3, 3))).reshape(n, 9)
+    C = (0.5 * rng.standard_normal((n, 9)))
+    params = np.stack([np.log(5e3) + 0.3 * rng.standard_normal(n), rng.uniform(0.2, 0.4, n), np.zeros(n)],
+                      axis=1).astype(np.float32)
+    vol = np.full(n, (0.5 * dx) ** 3, np.float32)
+    mid = np.zeros(n, np.int32)
+    frames = [10, 20, 30]
+    s = sim_mod.Simulator(R, dx, dt, (0.0, -9.8, 0.0), mats, ckpt_every=10)
+
+    def grads(x, target):
+        s.load(x.astype(np.float32), vol, mid, v=np.zeros((n, 3), np.float32), C=C.astype(np.float32),
+               F=F.astype(np.float32), params=params)
+        xs, prev = [], 0
+        for f in frames:
+            s.step(f - prev, record=True)
+            xs.append(s.positions().double().cpu().numpy())
+            prev = f
+        dLdx = 2.0 * (np.stack(xs) - target) / (len(frames) * n)
+        return s.backward(frames, torch.as_tensor(dLdx, dtype=torch.float32)).double().cpu().numpy()
+
+    grads(xa, xa[None] + 0.001)
+    st_a = s.stats()
+    assert 0 < st_a["tape_grid_blocks"] < st_a["pool_blocks"] and st_a["tape_grid_reruns"] == 0, st_a
+    target = xb[None] + np.array([0.0, -0.001, 0.0]) + 0.001 * rng.standard_normal((3, n, 3))
+    g = grads(xb, target)
+    st_b = s.stats()
+    assert st_b["tape_grid_reruns"] == 1 and st_b["tape_grid_blocks"] == st_b["pool_blocks"], st_b
+    s.close()
+    cfg = orc.Cfg((R, R, R), dx, dt, (0.0, -9.8, 0.0))
+    mat = orc.Material.from_table(vol, mid, mats, params)
+    _, tape = orc.run(cfg, orc.new_state(xb, np.zeros((n, 3), np.float32), C.astype(np.float32), F.astype(np.float32)),
+                      mat, 30, tape=True)
+    _, dLdx_ref = orc.trajectory_loss(tape[frames][:, :, 0:3], target)
+    _, g_ref = orc.backward(cfg, mat, tape, frames, dLdx_ref)
+    for j in range(2):
+        assert np.abs(g_ref[:, j]).max() > 0
+        assert rel(g[:, j], g_ref[:, j]) < GRAD_TOL, (j, rel(g[:, j], g_ref[:, j]))
