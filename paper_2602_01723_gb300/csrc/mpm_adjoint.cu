@@ -958,6 +958,33 @@ __global__ void k_inject_tab(int n, float4 *adj, const int *frame_first, const i
     }
 }
 
+// between two reverse substeps from the grid tape: clears the grid adjoint
+// of the substep just reversed (the active blocks counted in prev_ctr; NULL:
+// nothing to clear) and adds the loss gradient of every frame taken after
+// substep s0 + j + 1
+__global__ void k_adj_between(int n, float4 *adj, const int *frame_first, const int *frame_next, const SegParams *sp,
+                              int j, const unsigned *prev_ctr, unsigned max_active, float4 *gbar) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    if (prev_ctr) {
+        const unsigned total = min(prev_ctr[CTR_N_ACTIVE], max_active) * BLK_NODES;
+        for (unsigned i = tid; i < total; i += stride) gbar[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const long long sub = sp->s0 + j + 1;
+    const int f = frame_first[sub];
+    if (f < 0) return;
+    const float *base = sp->dldx;
+    for (int p = (int)tid; p < n; p += (int)stride) {
+        float4 a = adj[(size_t)p * ADJ_F4];
+        for (int g = f, guard = 0; g >= 0 && guard < 1 << 20; g = frame_next[g], ++guard) {
+            const float *dl = base + (size_t)g * n * 3;
+            a.x += dl[3 * p];
+            a.y += dl[3 * p + 1];
+            a.z += dl[3 * p + 2];
+        }
+        adj[(size_t)p * ADJ_F4] = a;
+    }
+}
+
 __global__ void k_export_grads(int n, const float4 *gpar, const float4 *adj, float *dparams, float *dstate0) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const float4 g = gpar[p];
@@ -1260,9 +1287,9 @@ static void tape_segment(mpm_ctx *ctx, int len, int bank, cudaStream_t st) {
     }
 }
 
-// reverse of one substep from a grid-tape slot: the adjoint kernels only
-static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *aout, cudaStream_t st) {
-    AdjointStore &A = ctx->adj;
+// the device context of a grid-tape slot: its records, binning, counters
+// and grid in place of the working ones (as grid buffer 0)
+static Dev slot_dev(mpm_ctx *ctx, const TapeSlot &T) {
     Dev Dj = ctx->D;
     Dj.rec = T.rec;
     Dj.sorted = T.sorted;
@@ -1273,25 +1300,39 @@ static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *
     Dj.page_epoch[0] = T.page_epoch;
     Dj.gmv[0] = T.gmv;
     Dj.gv[0] = T.gv;
+    return Dj;
+}
+
+// reverse of one substep from a grid-tape slot: the adjoint kernels only
+// (the grid adjoint it leaves is cleared by the next k_adj_between, or by
+// the segment's final clear)
+static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *aout, cudaStream_t st) {
+    AdjointStore &A = ctx->adj;
+    const Dev Dj = slot_dev(ctx, T);
     const int grid = ctx->grid_sub[1];
     k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(Dj, ain, aout, A.gpar, A.gbar);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
     k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(Dj, aout, A.gpar, A.gbar);
-    k_adj_clear<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
-    ctx->launches += 4;
+    ctx->launches += 3;
 }
 
-// reverse substeps len-1 .. 0 of a segment from grid-tape bank `bank`,
-// injecting the frame gradients from the device table
+// reverse substeps len-1 .. 0 of a segment from grid-tape bank `bank`;
+// before each, one launch clears the previous substep's grid adjoint and
+// injects the frame gradients from the device table.  Leaves the grid
+// adjoint zero.
 static void reverse_segment(mpm_ctx *ctx, int len, int bank, int cur, int pg, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
     const int n = ctx->D.n;
     for (int j = len - 1; j >= 0; --j) {
-        k_inject_tab<<<pg, 256, 0, st>>>(n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j);
+        const unsigned *prev = j + 1 < len ? tape_slot(ctx, bank, j + 1).ctr : nullptr;
+        k_adj_between<<<pg, 256, 0, st>>>(n, A.adj[cur], A.frame_first, A.frame_next, (const SegParams *)A.seg, j,
+                                          prev, ctx->D.max_active, A.gbar);
         ++ctx->launches;
         adjoint_taped(ctx, tape_slot(ctx, bank, j), A.adj[cur], A.adj[cur ^ 1], st);
         cur ^= 1;
     }
+    k_adj_clear<<<ctx->grid_small, 256, 0, st>>>(slot_dev(ctx, tape_slot(ctx, bank, 0)), A.gbar);
+    ++ctx->launches;
 }
 
 // One segment of the reverse pass without the grid tape, on the checkpoint
