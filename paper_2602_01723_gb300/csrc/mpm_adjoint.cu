@@ -1058,6 +1058,17 @@ __global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// resident CTAs per SM of the reverse G2P and P2G kernels (the smaller)
+int adjoint_occupancy() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_adj_g2p, ADJ_THREADS, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_adj_p2g, ADJ_THREADS, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return std::max(1, std::min(a, b));
+}
+
 void free_adjoint(AdjointStore &a) {
     for (float4 *p : a.ckpt)
         if (p) cudaFree(p);
@@ -1153,7 +1164,7 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);                       // P2G of the recorded state
     L_prepare(ctx, 0, -1, 0, st, 1);                   // v = mask(mv/m + dt g), keeping (mv, m)
-    const int grid = ctx->grid_sub[1];
+    const int grid = ctx->grid_adj;
     k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);
     k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
@@ -1309,7 +1320,7 @@ static Dev slot_dev(mpm_ctx *ctx, const TapeSlot &T) {
 static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *aout, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
     const Dev Dj = slot_dev(ctx, T);
-    const int grid = ctx->grid_sub[1];
+    const int grid = ctx->grid_adj;
     k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(Dj, ain, aout, A.gpar, A.gbar);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
     k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(Dj, aout, A.gpar, A.gbar);

@@ -443,6 +443,7 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
         ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->grid_small = ctx->sm_count * 8;
+    ctx->grid_adj = ctx->sm_count * adjoint_occupancy();
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         g_create_msg = std::string("create: ") + cudaGetErrorString(e);

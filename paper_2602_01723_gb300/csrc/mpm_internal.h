@@ -40,6 +40,7 @@ void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStr
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
 int substep_occupancy(int mode, int scatter, int chunk, bool xm);
 int substep_chunk_max();
+int adjoint_occupancy();
 
 // recorded trajectory and reverse-pass buffers
 struct AdjointStore {
@@ -117,6 +118,7 @@ struct mpm_ctx {
     int threads = 256;
     int grid_sub[3] = {0, 0, 0};
     int grid_small = 0;
+    int grid_adj = 0;             // reverse G2P / P2G kernels: SMs x resident CTAs per SM
     long long recorded = 0;       // substeps recorded since the last load / reset
     bool record_broken = false;
     mpm::AdjointStore adj;
