@@ -119,7 +119,10 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
  * the grid of each particle; params (n x 3 float: log E, nu, yield stress;
  * NULL: from the material table) overrides the table per particle.  Particle
  * mass is rho * vol.  Also clears the recorded trajectory.  Synchronises the
- * stream and reports out-of-range inputs. */
+ * stream and reports out-of-range inputs, except inside a stream capture (see
+ * mpm_backward), where the arrays must be device arrays, n must fit the
+ * capacity of an earlier load, and device errors surface at the next
+ * synchronising call. */
 MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, const float *v, const float *C,
                                       const float *F, const float *vol, const int32_t *material_id,
                                       const int32_t *instance, const float *params, void *stream);
@@ -127,7 +130,9 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
 /* Advances n_substeps >= 0 substeps.  With record != 0 the state at every
  * ckpt_every-th substep counted from the last load (or mpm_record_reset) is
  * kept for mpm_backward; the recording must be contiguous (record on every
- * call since the last reset).  Does not synchronise. */
+ * call since the last reset).  Does not synchronise.  Inside a stream capture
+ * the substeps are launched into the caller's graph; a recorded run needs
+ * the checkpoints of an earlier recorded run at least as long. */
 MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, void *stream);
 
 /* Copies the current state out, in the caller's particle order; any pointer
@@ -141,7 +146,18 @@ MPM_API mpm_status mpm_get_particles(mpm_ctx *ctx, float *x, float *v, float *C,
  * d/d log E, d/d nu, d/d yield stress, per particle; required) and, when not
  * NULL, dL_dstate0 (n x 24: the adjoint of the initial [x v C F]).  Recomputes
  * each checkpoint segment forward; the recorded state is left unchanged.
- * Synchronises the stream. */
+ * Synchronises the stream.
+ *
+ * Stream capture: a whole fwd+bwd (mpm_load_particles, mpm_step with record,
+ * mpm_get_particles, mpm_backward, mpm_reduce_by_material) may be captured
+ * into one CUDA graph by the caller.  Inside the capture nothing allocates
+ * or synchronises: call the same sequence once outside it first (it sizes
+ * the checkpoints, tapes and adjoint buffers); dL_dx and the outputs must be
+ * device arrays and n_frames <= 64.  A recorded state whose grid outgrows
+ * its tape slot, which outside a capture is rerun with larger slots, is then
+ * reported as MPM_ERR_CAPACITY by the next mpm_sync.  Replays reuse the
+ * host-side state of the capture: call nothing else on the context between
+ * replays that changes it. */
 MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const int32_t *frame_substep, const float *dL_dx,
                                 float *dL_dparams, float *dL_dstate0, void *stream);
 

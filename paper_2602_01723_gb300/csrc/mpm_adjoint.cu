@@ -985,6 +985,24 @@ __global__ void k_adj_between(int n, float4 *adj, const int *frame_first, const 
     }
 }
 
+// the frame table from a by-value list (no host copy, so that it can be
+// captured in a graph): per substep s <= S the first frame taken after s,
+// per frame the next one taken there; one CTA
+constexpr int FRAMES_BY_VALUE = 64;
+struct FrameList {
+    int n;
+    int sub[FRAMES_BY_VALUE];
+};
+__global__ void k_frame_table(FrameList fl, int *first, int *next, long long S) {
+    for (long long i = threadIdx.x; i <= S; i += blockDim.x) first[i] = -1;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int f = fl.n - 1; f >= 0; --f) {
+            next[f] = first[fl.sub[f]];
+            first[fl.sub[f]] = f;
+        }
+}
+
 __global__ void k_export_grads(int n, const float4 *gpar, const float4 *adj, float *dparams, float *dstate0) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         const float4 g = gpar[p];
@@ -1020,7 +1038,7 @@ struct TapeSlot {
 // *over and records an empty slot (no chunks, no blocks), whose reverse
 // kernels then do nothing; the host re-runs the reverse pass with larger
 // slots.
-__global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned *over) {
+__global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned *over, int strict) {
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
     const size_t n = (size_t)D.n;
     const unsigned n_all = min(D.ctr[CTR_N_ACTIVE + par], D.max_active);
@@ -1028,7 +1046,10 @@ __global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned 
     const unsigned n_act = fits ? n_all : 0u;
     const unsigned n_ch = fits ? min(D.ctr[CTR_N_CHUNKS], D.max_chunks) : 0u;
     const unsigned ep = D.ctr[CTR_EPOCH_OF + par];
-    if (tid == 0 && !fits) atomicOr(over, 1u);
+    if (tid == 0 && !fits) {
+        atomicOr(over, 1u);
+        if (strict) set_err(D, ERRB_CAPACITY);   // no rerun possible: reported as an error
+    }
     if (tid < CTR_COUNT) {
         unsigned v = D.ctr[tid];
         if (tid == CTR_N_ACTIVE) v = n_act;
@@ -1097,6 +1118,9 @@ static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
     const size_t bytes = (size_t)ctx->cap * REC_F4 * sizeof(float4);
     if (A.ckpt.size() <= c) A.ckpt.resize(c + 1, nullptr);
     if (!A.ckpt[c] || A.cap != ctx->cap) {
+        if (stream_capturing(st))
+            return ctx_fail(ctx, MPM_ERR_STATE, "inside a stream capture the checkpoints must exist from an earlier "
+                                                "recorded run at least as long");
         if (A.ckpt[c]) cudaFree(A.ckpt[c]);
         A.ckpt[c] = nullptr;
         cudaError_t e = cudaMalloc(&A.ckpt[c], bytes);
@@ -1289,7 +1313,8 @@ static void tape_segment(mpm_ctx *ctx, int len, int bank, cudaStream_t st) {
         const int par = s & 1;
         const bool more = s + 1 < len;
         L_prepare(ctx, par, more ? par ^ 1 : -1, s > 0, st, 1);
-        k_tape_save<<<ctx->grid_small, 256, 0, st>>>(ctx->D, par, tape_slot(ctx, bank, s), A.gt_pool, gt_over(ctx));
+        k_tape_save<<<ctx->grid_small, 256, 0, st>>>(ctx->D, par, tape_slot(ctx, bank, s), A.gt_pool, gt_over(ctx),
+                                                     A.strict ? 1 : 0);
         ++ctx->launches;
         if (more) {
             L_substep(ctx, 1, par, par ^ 1, st);
@@ -1459,7 +1484,8 @@ static cudaGraphExec_t job_graph(mpm_ctx *ctx, const RevJob &J, int pg, long lon
 // runs one step: its graph where graphs are in use, else directly
 static mpm_status run_step(mpm_ctx *ctx, const RevJob &J, int pg, cudaStream_t st) {
     long long per = 0;
-    cudaGraphExec_t ex = (ctx->use_graph && !ctx->trace_on) ? job_graph(ctx, J, pg, per) : nullptr;
+    // inside the caller's capture the step's kernels go straight into its graph
+    cudaGraphExec_t ex = (ctx->use_graph && !ctx->trace_on && !ctx->adj.strict) ? job_graph(ctx, J, pg, per) : nullptr;
     if (!ex) return run_job(ctx, J, pg, st);
     if (cudaGraphLaunch(ex, st) != cudaSuccess) {
         cudaGetLastError();
@@ -1492,6 +1518,21 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
     const size_t n = (size_t)D.n;
     const long long k = ctx->opt.ckpt_every;
     mpm_status s;
+    // Inside the caller's stream capture nothing may allocate or synchronise:
+    // the buffers come from an earlier call outside the capture, inputs and
+    // outputs are device arrays, and a grid-tape overflow (which cannot be
+    // rerun inside a graph) is reported as a device capacity error.
+    const bool cap = stream_capturing(st);
+    A.strict = cap;
+    const char *warm = "inside a stream capture, call mpm_backward once outside it first with the same sizes "
+                       "(it allocates its buffers then)";
+    if (cap && (!is_device_ptr(dL_dparams) || (dL_dstate0 && !is_device_ptr(dL_dstate0)) ||
+                (n_frames > 0 && !is_device_ptr(dL_dx)) || n_frames > FRAMES_BY_VALUE))
+        return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "inside a stream capture dL_dx and the outputs must be device "
+                                                  "arrays, and there may be at most 64 frames");
+    if (cap && (A.cap_adj != ctx->cap || A.pool != ctx->pool_blocks || A.frame_first_cap < S + 1 ||
+                A.frame_cap < std::max(n_frames, 1) || !A.seg))
+        return ctx_fail(ctx, MPM_ERR_STATE, warm);
     if (A.cap_adj != ctx->cap) {
         if ((s = dev_alloc(ctx, &A.adj[0], (size_t)ctx->cap * ADJ_F4)) || (s = dev_alloc(ctx, &A.adj[1], (size_t)ctx->cap * ADJ_F4)) ||
             (s = dev_alloc(ctx, &A.gpar, (size_t)ctx->cap)) || (s = dev_alloc(ctx, &A.final_state, (size_t)ctx->cap * REC_F4))) {
@@ -1507,7 +1548,16 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
             return ctx_fail(ctx, MPM_ERR_CUDA, "memset");
     }
     const size_t tape_states = (size_t)std::min<long long>(k, S);
-    bool use_gt = ctx->opt.tape_grid == 0 && ensure_grid_tape(ctx, tape_states, st);
+    if (cap) {
+        // use what an earlier call left: no allocation here
+        const long long shape[3] = {ctx->cap, (long long)ctx->chunk_cap, ctx->total_blocks};
+        const bool gt_ok = ctx->opt.tape_grid == 0 && A.gt && A.gt_bank_states >= tape_states &&
+                           std::equal(shape, shape + 3, A.gt_shape);
+        const bool tape_ok = A.tape && A.tape_states >= tape_states && A.tape_cap == ctx->cap;
+        if (!gt_ok && !tape_ok) return ctx_fail(ctx, MPM_ERR_STATE, warm);
+    }
+    bool use_gt = ctx->opt.tape_grid == 0 && (cap ? (A.gt && A.gt_bank_states >= tape_states)
+                                                   : ensure_grid_tape(ctx, tape_states, st));
     if (ctx->opt.tape_grid != 0 && A.gt) {
         cudaFree(A.gt);
         A.gt = nullptr;
@@ -1522,9 +1572,11 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         return MPM_OK;
     };
     if (use_gt) {
-        if (A.tape) cudaFree(A.tape);   // the grid tape holds the records too
-        A.tape = nullptr;
-        A.tape_states = 0;
+        if (A.tape && !cap) {
+            cudaFree(A.tape);   // the grid tape holds the records too
+            A.tape = nullptr;
+            A.tape_states = 0;
+        }
     } else if ((s = ensure_record_tape())) {
         return s;
     }
@@ -1558,7 +1610,13 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
             return ctx_fail(ctx, MPM_ERR_OOM, "reverse-pass allocation failed");
         }
     }
-    {
+    if (n_frames <= FRAMES_BY_VALUE) {
+        FrameList fl;
+        fl.n = n_frames;
+        for (int f = 0; f < n_frames; ++f) fl.sub[f] = frame_substep[f];
+        k_frame_table<<<1, 256, 0, st>>>(fl, A.frame_first, A.frame_next, S);
+        ++ctx->launches;
+    } else {
         std::vector<int> first((size_t)S + 1, -1), next((size_t)std::max(n_frames, 1), -1);
         for (int f = n_frames - 1; f >= 0; --f) {
             next[f] = first[frame_substep[f]];
@@ -1634,6 +1692,7 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
         return ctx_fail(ctx, MPM_ERR_CUDA, "state restore");
     rebin(ctx, st);
     if (cudaGetLastError() != cudaSuccess) return ctx_fail(ctx, MPM_ERR_CUDA, "reverse-pass launch failed");
+    if (cap) return MPM_OK;   // errors surface at the next synchronising call (mpm_sync)
     if ((s = ctx_check(ctx, st))) return s;
     if (!use_gt) return MPM_OK;
     unsigned over = 0;

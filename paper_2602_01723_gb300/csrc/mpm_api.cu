@@ -79,6 +79,15 @@ bool mpm::is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+bool mpm::stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs == cudaStreamCaptureStatusActive;
+}
+
 namespace {
 
 mpm_status status_from_err(mpm_ctx *ctx, unsigned err) {
@@ -107,6 +116,7 @@ mpm_status stage_in(mpm_ctx *ctx, const void *src, size_t bytes, size_t &off, co
     *dev = nullptr;
     if (!src) return MPM_OK;
     if (is_device_ptr(src)) { *dev = src; return MPM_OK; }
+    if (stream_capturing(st)) return fail(ctx, MPM_ERR_INVALID_ARG, "inside a stream capture the inputs must be device arrays");
     off = (off + 255) & ~size_t(255);
     if (off + bytes > ctx->stage_bytes) return fail(ctx, MPM_ERR_CUDA, "internal: staging buffer too small");
     void *d = (char *)ctx->stage + off;
@@ -274,7 +284,8 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, 
     L_substep(ctx, 0, 0, 0, st);
     int s = 0;
     const int middle = n_sub - 1;
-    if (ctx->use_graph && !ctx->trace_on && !tape && middle >= 4) {
+    // inside the caller's stream capture the substeps go straight into its graph
+    if (ctx->use_graph && !ctx->trace_on && !tape && middle >= 4 && !stream_capturing(st)) {
         cudaGraphExec_t ex = graph_pair(ctx, st);
         if (ex) {
             for (; s + 1 < middle; s += 2) {
@@ -463,6 +474,9 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     if (n <= 0 || n > (1ll << 31) - 1 || !x || !vol || !material_id)
         return fail(ctx, MPM_ERR_INVALID_ARG, "n must be in [1, 2^31) and x, vol, material_id non-NULL");
     cudaStream_t st = S(stream);
+    const bool cap = stream_capturing(st);
+    if (cap && (n > ctx->cap || !ctx->D.rec))
+        return fail(ctx, MPM_ERR_STATE, "inside a stream capture n must fit the capacity of an earlier load");
     mpm_status s = ensure_particles(ctx, n);
     if (s) return s;
     Dev &D = ctx->D;
@@ -491,6 +505,7 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     ctx->loaded = true;
     ctx->recorded = 0;
     ctx->record_broken = false;
+    if (cap) return MPM_OK;   // device errors surface at the next synchronising call
     s = check_device_error(ctx, st);
     if (s) ctx->loaded = false;
     return s;

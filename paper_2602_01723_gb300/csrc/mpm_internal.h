@@ -80,6 +80,7 @@ struct AdjointStore {
     long long gt_shape[4] = {0, 0, 0, 0};
     long long gt_gen = 0;           // counts grid-tape allocations (part of the graph keys)
     long long gt_reruns = 0;        // reverse passes run again after a grid-tape overflow
+    bool strict = false;            // the reverse pass is being captured by the caller: no reruns
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // CUDA graphs of the reverse pass's steps, keyed by their shape (segment
@@ -171,4 +172,6 @@ mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);
 mpm_status ctx_check(mpm_ctx *ctx, cudaStream_t st);
 bool is_device_ptr(const void *p);
+// the stream is being captured into a CUDA graph (by the caller)
+bool stream_capturing(cudaStream_t st);
 }  // namespace mpm
