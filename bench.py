@@ -434,6 +434,40 @@ def bgdo_leg(args, sim, sc, init, flush):
             "note": "CUDA events, medians; stage 1 includes the three snapshot copies"}
 
 
+def one_graph_fwd_bwd(sim, prm0, init, frames, target, flush, units, ref):
+    """The whole fwd+bwd (load, recorded forward, frame positions, loss,
+    reverse pass, per-material reduction) captured once into one CUDA graph
+    with torch.cuda.graph, then replayed: CUDA events around each replay."""
+    import torch
+    from paper_2602_01723_gb300.sim import trajectory
+    p = prm0.clone().requires_grad_(True)
+
+    def fbg():
+        xs = trajectory(p, sim, init, frames)
+        (g,) = torch.autograd.grad(((xs - target) ** 2).sum(), p)
+        return sim.reduce_by_material(g)
+    fbg()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out = fbg()
+    ms = []
+    for k in range(3):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    sim.sync()
+    t = statistics.median(ms)
+    rel = float((out - ref).abs().max() / ref.abs().max())
+    del graph
+    return {"ms": t, "value": units / (t * 1e-3), "unit": UNIT, "max_rel_diff_vs_eager": rel}
+
+
 def configs_leg(args, dev, flush):
     """Forward throughput of the other workload shapes (the 8k cube, the
     64-instance batch on its own 64^3 grids, the 2M-particle 256^3
@@ -506,11 +540,18 @@ def configs_leg(args, dev, flush):
                 torch.cuda.synchronize()
                 fms.append(e0.elapsed_time(e1))
             tf = statistics.median(fms)
+            one_graph = None
+            if name == "batch_64":
+                try:
+                    one_graph = one_graph_fwd_bwd(sim, prm0, init, frames, target, flush, n * S, fb())
+                except Exception as e:  # noqa: BLE001 -- reported in the line
+                    one_graph = {"error": "%s: %s" % (type(e).__name__, e)}
             free1, _ = torch.cuda.mem_get_info()
             out[name]["fwd_bwd"] = {"ms": tf, "value": n * S / (tf * 1e-3), "unit": UNIT,
                                     "ckpt_every": int(sc.ckpt_every or 20), "frames": len(frames),
                                     "grads_finite": bool(torch.isfinite(g).all().item()),
                                     "grads": "per instance" if sc.n_instances > 1 else "per object (material id)",
+                                    "one_cuda_graph": one_graph,
                                     "device_memory_gb": (free0 - free1) / 1e9,
                                     "device_memory": "cudaMemGetInfo after the fwd+bwd runs minus before the context "
                                                      "was created: the context (state, grids, checkpoints, tapes, "
