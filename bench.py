@@ -499,6 +499,12 @@ def configs_leg(args, dev, flush):
             L.mpm_load_particles(sim.ctx, n, _p(x0), _p(v0), None, None, _p(vol), _p(mid), _p(inst), _p(prm),
                                  _stream())
             sim.step(S)
+        tuned = None
+        if name == "batch_64":
+            # the batch runs with autotuned tile sizes (scatter strategy, chunk)
+            L.mpm_load_particles(sim.ctx, n, _p(x0), _p(v0), None, None, _p(vol), _p(mid), _p(inst), _p(prm),
+                                 _stream())
+            tuned = sim.autotune(20)
         run()
         sim.sync()
         ms = []
@@ -513,6 +519,7 @@ def configs_leg(args, dev, flush):
             ms.append(e0.elapsed_time(e1))
         t = statistics.median(ms)
         out[name] = {"particles": n, "substeps": S, "ms": t, "value": n * S / (t * 1e-3), "unit": UNIT,
+                     "autotuned": tuned,
                      "hbm_frac": n * S / (t * 1e-3) * FWD_BYTES_PER_PS / 1e9 / load_peaks()[0]}
         if name in ("batch_64", "large_2m"):
             frames = [int(f) for f in (np.linspace(S / 10, S, 10) if sc.frame_sub is None else sc.frame_sub)]
