@@ -297,7 +297,12 @@ __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep
 //      to global memory and a 16-float scatter packet replaces the staged
 //      record; the particle is binned for the next substep;
 //   B. packets are scattered into the 8^3-node tile (nodes 4B-1 .. 4B+6) and
-//      the tile is flushed with one vector reduction per touched node.
+//      the tile is flushed with one vector reduction per touched node.  With
+//      the fixed-point tile the warps take the packets ordered by (rank
+//      within bank, bank of the base node): one loop iteration moves every
+//      lane by the same node offset, so lanes with distinct base banks hit
+//      distinct banks in all 108 atomics, and the first warps of a chunk see
+//      at most two-way conflicts.
 // SCAT selects the scatter of phase B: 0 = float shared-memory atomics;
 // 1 = int32 fixed-point shared-memory atomics with a per-chunk scale (native
 // integer atomics; the scale keeps the rounding below 2^-30 of the chunk's
@@ -342,6 +347,11 @@ template <int TPB> struct SubstepSmem {
     int slot_s[2][27];               // pool slot of blocks (B-1 .. B+1)^3 in the scatter grid, per chunk parity
     float red[2 * (TPB / 32)];
     float scale[2];
+    int ccount[32];                  // packets per bank of their base node (scatter order)
+    int ptab[TPB];                   // packets of rank < r
+    unsigned mtab[TPB];              // banks holding a packet of rank r
+    int prank[TPB], pcol[TPB];       // each packet's bank and rank within it
+    int perm[TPB];                   // scatter order: packets by (rank, bank)
 };
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -445,6 +455,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
     }
     if (SCATTER && SCAT != 2)
         for (int t = tid; t < 4 * ST3P; t += T) S.t.i[t] = 0;
+    if (tid < 32) S.ccount[tid] = 0;
     __syncthreads();
     stage_level2<TPB, GATHER, SCATTER>(D, S, S.cd[0], gpar, spar, ep_g, ep_s);
     cp_async_commit();
@@ -684,6 +695,17 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
             }
         }
 
+        if (SCATTER && SCAT == 1 && tid < cnt) {
+            // bank of the packet's base node: every node of its stencil is the
+            // base plus an offset common to all packets in one loop iteration,
+            // and the tile's component stride is a multiple of 32 banks
+            const float4 q = S.pk[tid * PK_F4];
+            int col = 0;
+            if (q.w > 0.f)
+                col = tidx((int)floorf(q.x - 0.5f), (int)floorf(q.y - 0.5f), (int)floorf(q.z - 0.5f)) & 31;
+            S.pcol[tid] = col;
+            S.prank[tid] = atomicAdd(&S.ccount[col], 1);
+        }
         if (SCATTER && SCAT == 1) {
             // per-chunk fixed-point scales from the sums of the per-particle bounds
 #pragma unroll
@@ -697,6 +719,21 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
         // gather-tile buffers, so level 3 of chunk c + G goes in flight now
         cp_async_wait_all();
         __syncthreads();
+        if (SCATTER && SCAT == 1) {
+            // per rank level r: the packets of lower rank, and the banks with a packet of rank r
+            const int lane = tid & 31, w = tid >> 5;
+            const int cc = S.ccount[lane];
+            int mx = cc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            for (int rr = w; rr < mx; rr += T / 32) {
+                const unsigned m = __ballot_sync(0xffffffffu, cc > rr);
+                int sm = min(cc, rr);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+                if (lane == 0) { S.mtab[rr] = m; S.ptab[rr] = sm; }
+            }
+        }
         if (has_next) {
             if (SCATTER) stage_slots<TPB>(S, (kc + 1) & 1, ep_s);
             stage_level3<TPB, GATHER>(D, S, S.cd[(kc + 1) % 3], gpar, ep_g);
@@ -710,7 +747,15 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 S.scale[0] = bm > 0.f ? 1073741824.f / bm : 1.f;     // 2^30 / bound
                 S.scale[1] = bv > 0.f ? 1073741824.f / bv : 1.f;
             }
-            if (SCAT == 1) __syncthreads();
+            if (SCAT == 1) {
+                __syncthreads();
+                if (tid < cnt) {
+                    const int r = S.prank[tid], k = S.pcol[tid];
+                    S.perm[S.ptab[r] + __popc(S.mtab[r] & ((1u << k) - 1u))] = tid;
+                }
+                if (tid < 32) S.ccount[tid] = 0;
+                __syncthreads();
+            }
             const float sc_m = SCAT == 1 ? S.scale[0] : 1.f, sc_v = SCAT == 1 ? S.scale[1] : 1.f;
 
             // ---- B. scatter packets -------------------------------------------
@@ -719,8 +764,14 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
             const int span = rounds * (T >> 5);
             for (int r = 0; r < rounds; ++r) {
                 const int u = r * T + tid;
-                const int j = (u & 31) * span + (u >> 5);
-                if (j >= cnt) continue;
+                int j;
+                if (SCAT == 1) {
+                    if (u >= cnt) continue;
+                    j = S.perm[u];   // warps take packets by (rank, bank): few bank conflicts
+                } else {
+                    j = (u & 31) * span + (u >> 5);
+                    if (j >= cnt) continue;
+                }
                 const float4 q0 = S.pk[j * PK_F4];
                 if (!(q0.w > 0.f)) continue;
                 const float4 q1r = S.pk[j * PK_F4 + 1], q2 = S.pk[j * PK_F4 + 2], q3 = S.pk[j * PK_F4 + 3],

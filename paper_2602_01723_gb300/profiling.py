@@ -130,7 +130,7 @@ def kernel(rep, out_md, cmd, traffic_key=None, particles=None):
         b = sum(per_launch) / len(per_launch)
         d[traffic_key] = {"bytes_per_launch": b, "source_hash": source_hash(), "launches": len(per_launch),
                           "particles": particles, "note": "dram__bytes_read.sum + dram__bytes_write.sum, "
-                          "ncu --set full (cold L2 per replay)"}
+                          "ncu --set full (cold L2 per replay)", "hashed_sources": list(KERNEL_SOURCES)}
         with open(TRAFFIC, "w") as f:
             json.dump(d, f, indent=1)
 
