@@ -32,7 +32,7 @@ namespace {
 thread_local std::string g_mcis_msg;
 
 constexpr double WSCALE = 1099511627776.0;   // 2^40
-constexpr int RINGS = 3;                      // cell edge >= d_cut / 3: rings 0..3 cover d_cut
+constexpr int RINGS = 6;                      // cell edge >= d_cut / 6: rings 0..6 cover d_cut
 
 __device__ __forceinline__ int find_range(const int64_t *off, int n, int64_t i) {
     int lo = 0, hi = n;   // off[lo] <= i < off[hi]
@@ -199,10 +199,11 @@ __global__ void k_mc_cand_scatter(int n_obj, const int64_t *coff, const float *c
     }
 }
 
-// squared distance from q to the box of cell c (cells of edge h from the origin)
-__device__ __forceinline__ double box_d2(double q, int c, double h) {
-    const double lo = c * h, hi = lo + h;
-    const double e = q < lo ? lo - q : (q > hi ? q - hi : 0.0);
+
+// squared distance along one axis from q to cell c of edge h, in FP32
+__device__ __forceinline__ float box_d2f(float q, int c, float h) {
+    const float lo = (float)c * h, hi = lo + h;
+    const float e = q < lo ? lo - q : (q > hi ? q - hi : 0.f);
     return e * e;
 }
 
@@ -212,6 +213,7 @@ __global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, const
                         double *d, double *w, long long *wq) {
     const int64_t n = coff[n_obj];
     const double h = 1.0 / (double)g.inv_h;
+    const float hf = 1.f / g.inv_h;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t j = order[t];
         const int k = find_range(coff, n_obj, j);
@@ -219,24 +221,31 @@ __global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, const
         const int cx = cell_of(qx, g.inv_h, g.G), cy = cell_of(qy, g.inv_h, g.G), cz = cell_of(qz, g.inv_h, g.G);
         const long long base = (long long)k * g.cells;
         double best = INFINITY;
+        float screen = INFINITY;   // best * (1 + 1e-6), rounded up to FP32
         for (int r = 0; r <= RINGS; ++r) {
             // cells of ring r lie at least (r - 1) h away: stop once the best is closer
             const double lb = (double)(r - 1) * h;
             if (r > 1 && best <= lb * lb) break;
+            // pruning threshold in FP32: the FP32 box distance of a cell within d_cut is
+            // within 1.3e-7 of the exact one (cell edges and differences rounded), so this
+            // margin never skips a cell that could hold a closer point
+            const float prune = (float)best * 1.00001f + 2e-7f;
             for (int ix = -r; ix <= r; ++ix) {
                 const int x = cx + ix;
                 if (x < 0 || x >= g.G) continue;
                 for (int iy = -r; iy <= r; ++iy) {
                     const int y = cy + iy;
                     if (y < 0 || y >= g.G) continue;
-                    for (int iz = -r; iz <= r; ++iz) {
-                        if (max(abs(ix), max(abs(iy), abs(iz))) != r) continue;   // ring r only
+                    // ring r only: the whole row on its x or y faces, else its two z ends
+                    const bool face = ix == -r || ix == r || iy == -r || iy == r;
+                    const int zstep = (face || r == 0) ? 1 : 2 * r;
+                    for (int iz = -r; iz <= r; iz += zstep) {
                         const int z = cz + iz;
                         if (z < 0 || z >= g.G) continue;
                         // a cell wholly farther than the best point holds nothing closer
                         // (cells are clamped at the cube's faces, so only interior cells are skipped)
                         if (x > 0 && y > 0 && z > 0 && x < g.G - 1 && y < g.G - 1 && z < g.G - 1 &&
-                            box_d2(qx, x, h) + box_d2(qy, y, h) + box_d2(qz, z, h) > best)
+                            box_d2f(qx, x, hf) + box_d2f(qy, y, hf) + box_d2f(qz, z, hf) > prune)
                             continue;
                         const long long key = base + ((long long)x * g.G + y) * g.G + z;
                         const unsigned s0 = start[key], s1 = s0 + cnt[key];
@@ -244,12 +253,16 @@ __global__ void k_mc_nn(int n_obj, const int64_t *coff, const float *cand, const
                             const float4 c = sorted[s];
                             const float ex = qx - c.x, ey = qy - c.y, ez = qz - c.z;
                             const float d2f = ex * ex + ey * ey + ez * ez;
-                            // the FP32 value is within 1e-6 relative of the exact one
-                            if ((double)d2f <= best * (1.0 + 1e-6)) {
+                            // the FP32 value is within 1e-6 relative of the exact one, so a
+                            // point closer than best passes this FP32 screen
+                            if (d2f <= screen) {
                                 const double fx = (double)qx - (double)c.x, fy = (double)qy - (double)c.y,
                                              fz = (double)qz - (double)c.z;
                                 const double d2 = fx * fx + fy * fy + fz * fz;
-                                if (d2 < best) best = d2;
+                                if (d2 < best) {
+                                    best = d2;
+                                    screen = __double2float_ru(best * (1.0 + 1e-6));
+                                }
                             }
                         }
                     }
