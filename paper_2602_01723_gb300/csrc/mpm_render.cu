@@ -89,37 +89,58 @@ __global__ void k_rd_pre(long long n, const float *mean, const float *cov, const
     }
 }
 
-// exclusive scan of n counts in one CTA; total written to *total
-__global__ void __launch_bounds__(1024) k_rd_scan(const unsigned *in, unsigned *out, long long n,
-                                                  unsigned long long *total) {
-    __shared__ unsigned long long sh[32];
-    unsigned long long carry = 0;
+// exclusive scan of n unsigned counts over many CTAs, three phases:
+//   1. each CTA scans its 1024 counts and stores their sum in btot[block];
+//   2. one CTA scans the block sums (exclusive, in place) and writes the
+//      grand total to *total;
+//   3. each CTA adds its block's offset.
+constexpr int SC_T = 1024;
+__device__ __forceinline__ unsigned long long block_exclusive_scan(unsigned long long v, unsigned long long &tot) {
+    __shared__ unsigned long long sh[SC_T / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (long long b0 = 0; b0 < n; b0 += blockDim.x) {
-        const long long i = b0 + threadIdx.x;
-        const unsigned long long v = i < n ? in[i] : 0ull;
-        unsigned long long x = v;
+    unsigned long long x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
         }
-        if (lane == 31) sh[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            unsigned long long t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0ull;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            sh[lane] = t;
-        }
-        __syncthreads();
-        if (i < n) out[i] = (unsigned)(carry + (w > 0 ? sh[w - 1] : 0ull) + x - v);
-        const unsigned long long tot = sh[(blockDim.x >> 5) - 1];
-        __syncthreads();
+        sh[lane] = t;
+    }
+    __syncthreads();
+    const unsigned long long ex = (w > 0 ? sh[w - 1] : 0ull) + x - v;
+    tot = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return ex;
+}
+__global__ void __launch_bounds__(SC_T) k_sc_block(const unsigned *in, unsigned *out, long long n,
+                                                   unsigned long long *btot) {
+    const long long i = blockIdx.x * (long long)SC_T + threadIdx.x;
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan(i < n ? in[i] : 0u, tot);
+    if (i < n) out[i] = (unsigned)ex;
+    if (threadIdx.x == 0) btot[blockIdx.x] = tot;
+}
+__global__ void __launch_bounds__(SC_T) k_sc_totals(unsigned long long *btot, long long nb, unsigned long long *total) {
+    unsigned long long carry = 0;
+    for (long long b0 = 0; b0 < nb; b0 += SC_T) {
+        const long long i = b0 + threadIdx.x;
+        unsigned long long tot;
+        const unsigned long long ex = block_exclusive_scan(i < nb ? btot[i] : 0ull, tot);
+        if (i < nb) btot[i] = carry + ex;
         carry += tot;
     }
     if (threadIdx.x == 0) *total = carry;
+}
+__global__ void __launch_bounds__(SC_T) k_sc_add(unsigned *out, long long n, const unsigned long long *btot) {
+    const long long i = blockIdx.x * (long long)SC_T + threadIdx.x;
+    if (i < n) out[i] += (unsigned)btot[blockIdx.x];
 }
 
 // 2. one key per touched tile
@@ -256,6 +277,16 @@ bool is_dev(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// exclusive scan of n counts into out (sums below 2^32), grand total to *total;
+// btot: ceil(n / SC_T) scratch words
+void scan_counts(const unsigned *in, unsigned *out, long long n, unsigned long long *btot, unsigned long long *total,
+                 cudaStream_t st) {
+    const long long nb = (n + SC_T - 1) / SC_T;
+    if (nb > 0) k_sc_block<<<(unsigned)nb, SC_T, 0, st>>>(in, out, n, btot);
+    k_sc_totals<<<1, SC_T, 0, st>>>(btot, nb, total);
+    if (nb > 0) k_sc_add<<<(unsigned)nb, SC_T, 0, st>>>(out, n, btot);
+}
+
 int blocks_for(long long n, int t) {
     long long b = (n + t - 1) / t;
     if (b < 1) b = 1;
@@ -313,6 +344,7 @@ extern "C" MPM_API mpm_status mpm_render(int64_t n, const float *mean, const flo
         const size_t o_cnt = off; off += al(n * 4);
         const size_t o_off = off; off += al(n * 4);
         const size_t o_tot = off; off += al(8);
+        const size_t o_bt = off; off += al(((n + SC_T - 1) / SC_T + 1) * 8);
         const size_t o_rng = off; off += al(tiles * 8);
         const size_t o_img = off; off += al(npix * 12);
         const size_t o_tr = off; off += al(npix * 4);
@@ -337,7 +369,7 @@ extern "C" MPM_API mpm_status mpm_render(int64_t n, const float *mean, const flo
         RD_CK(cudaMemsetAsync(dtot, 0, 8, st));
         if (n > 0) {
             k_rd_pre<<<blocks_for(n, 256), 256, 0, st>>>(n, dmean, dcov, dop, c, g0, g1, rect, cnt);
-            k_rd_scan<<<1, 1024, 0, st>>>(cnt, offs, n, dtot);
+            scan_counts(cnt, offs, n, (unsigned long long *)P(o_bt), dtot, st);
             RD_CK(cudaGetLastError());
             RD_CK(cudaMemcpyAsync(&total, dtot, 8, cudaMemcpyDeviceToHost, st));
             RD_CK(cudaStreamSynchronize(st));
@@ -354,6 +386,7 @@ extern "C" MPM_API mpm_status mpm_render(int64_t n, const float *mean, const flo
             const size_t o_h = ko; ko += al((size_t)256 * nb * 4);
             const size_t o_ho = ko; ko += al((size_t)256 * nb * 4);
             const size_t o_ht = ko; ko += al(8);
+            const size_t o_hb = ko; ko += al(((256ll * nb + SC_T - 1) / SC_T + 1) * 8);
             if (cudaMallocAsync((void **)&kbuf, ko, st) != cudaSuccess) {
                 cudaGetLastError();
                 kbuf = nullptr;
@@ -371,7 +404,7 @@ extern "C" MPM_API mpm_status mpm_render(int64_t n, const float *mean, const flo
             const int bits = 32 + tile_bits;
             for (int shift = 0; shift < bits; shift += 8) {
                 k_rs_hist<<<nb, RS_THREADS, 0, st>>>(k0, nk, shift, hist, nb);
-                k_rd_scan<<<1, 1024, 0, st>>>(hist, hoff, (long long)256 * nb, htot);
+                scan_counts(hist, hoff, (long long)256 * nb, (unsigned long long *)(kbuf + o_hb), htot, st);
                 k_rs_scatter<<<nb, RS_THREADS, 0, st>>>(k0, v0, nk, shift, hoff, nb, k1, v1);
                 RD_CK(cudaGetLastError());
                 unsigned long long *tk = k0; k0 = k1; k1 = tk;
