@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/mpm.h"
+#include "mpm_scan.cuh"
 
 namespace {
 
@@ -76,39 +77,6 @@ __global__ void k_mc_scatter(int n_obj, const int64_t *soff, const float *surf, 
             (long long)k * g.cells +
             ((long long)cell_of(x, g.inv_h, g.G) * g.G + cell_of(y, g.inv_h, g.G)) * g.G + cell_of(z, g.inv_h, g.G);
         sorted[start[key] + rank[s]] = make_float4(x, y, z, 0.f);
-    }
-}
-
-// exclusive scan of n unsigned counts in one CTA (n up to a few million: a
-// strided loop of block scans)
-__global__ void __launch_bounds__(1024) k_mc_scan_u32(const unsigned *in, unsigned *out, long long n) {
-    __shared__ unsigned sh[32];
-    unsigned carry = 0;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (long long b = 0; b < n; b += blockDim.x) {
-        const long long i = b + threadIdx.x;
-        const unsigned v = i < n ? in[i] : 0u;
-        unsigned x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) sh[w] = x;
-        __syncthreads();
-        if (w == 0) {
-            unsigned t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0u;
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-            sh[lane] = t;
-        }
-        __syncthreads();
-        const unsigned before = (w > 0 ? sh[w - 1] : 0u) + carry;
-        if (i < n) out[i] = before + x - v;
-        const unsigned total = sh[(blockDim.x >> 5) - 1];
-        __syncthreads();
-        carry += total;
     }
 }
 
@@ -370,6 +338,8 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
     const size_t o_wq = off; off += al(nc * 8);
     const size_t o_cum = off; off += al(nc * 8);
     const size_t o_tot = off; off += al((nb + 1) * 8);
+    const size_t o_kb = off; off += al(((keys + SC_T - 1) / SC_T + 1) * 8);   // cell-count scan block sums
+    const size_t o_kt = off; off += al(8);
     const size_t o_d = off; off += al(nc * 8);
     const size_t o_w = off; off += al(nc * 8);
     const size_t o_pick = off; off += al(nd * 8);
@@ -408,7 +378,7 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
             k_mc_count<<<blocks_for(ns, 256), 256, 0, st>>>(n_obj, dsoff, dsurf, g, cnt, rank);
             MC_CK(cudaGetLastError());
         }
-        k_mc_scan_u32<<<1, 1024, 0, st>>>(cnt, start, keys);
+        scan_counts(cnt, start, keys, (unsigned long long *)P(o_kb), (unsigned long long *)P(o_kt), st);
         MC_CK(cudaGetLastError());
         if (ns > 0) {
             k_mc_scatter<<<blocks_for(ns, 256), 256, 0, st>>>(n_obj, dsoff, dsurf, g, start, rank, sorted);
@@ -421,7 +391,7 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
             unsigned *crank = (unsigned *)P(o_crank), *order = (unsigned *)P(o_order);
             MC_CK(cudaMemsetAsync(cnt2, 0, keys * 4, st));
             k_mc_cand_count<<<blocks_for(nc, 256), 256, 0, st>>>(n_obj, dcoff, dcand, g, cnt2, crank);
-            k_mc_scan_u32<<<1, 1024, 0, st>>>(cnt2, start2, keys);
+            scan_counts(cnt2, start2, keys, (unsigned long long *)P(o_kb), (unsigned long long *)P(o_kt), st);
             k_mc_cand_scatter<<<blocks_for(nc, 256), 256, 0, st>>>(n_obj, dcoff, dcand, g, start2, crank, order);
             MC_CK(cudaGetLastError());
             k_mc_nn<<<blocks_for(nc, 128), 128, 0, st>>>(n_obj, dcoff, dcand, order, g, start, cnt, sorted, sigma, eps,
