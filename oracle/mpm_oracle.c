@@ -30,9 +30,11 @@
  *     (§3.2, with Sigma = R S S^T R^T of §3.1);
  *   - MCIS fill sampling (§4.1) and the splatting of the Gaussians into an
  *     image (§3.1).
- * Readings where the paper is silent are listed in the design doc (interpolation
- * kernel = quadratic B-spline, walls, SVD sign convention, the Drucker-Prager
- * delta-gamma of Klar et al. 2016, the 1e-4 floor before log).
+ * Where the paper is silent this code reads it as follows: the interpolation
+ * kernel is the quadratic B-spline; walls are a 3-node band per face (sticky
+ * floor, slip elsewhere); the SVD has det U = det V = +1 with the sign of
+ * det F on the smallest singular value; the Drucker-Prager delta-gamma is
+ * that of Klar et al. 2016; singular values are floored at 1e-4 before log.
  *
  * Matrices are 3x3 row-major doubles.  Grids are dense, node (I,J,K) at
  * ((I*res1)+J)*res2+K, positions I*dx.
