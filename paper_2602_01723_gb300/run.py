@@ -20,7 +20,13 @@ def main():
     ap.add_argument("--record", action="store_true", help="record checkpoints for a reverse pass")
     ap.add_argument("--backward", action="store_true",
                     help="record the run, then time the reverse pass of a loss on the final positions")
+    ap.add_argument("--mcis", action="store_true",
+                    help="instead: MCIS fill sampling of the three objects (750k candidates), twice")
+    ap.add_argument("--render", action="store_true",
+                    help="instead: splat the scene's Gaussians (deformed by a stressed key frame) at 1024x768, twice")
     args = ap.parse_args()
+    if args.mcis or args.render:
+        return other(args)
 
     import torch
     from . import scenes
@@ -51,6 +57,50 @@ def main():
         st["backward_ms"] = e[1].elapsed_time(e[2])
     print(json.dumps(st))
     s.close()
+
+
+def other(args):
+    """One MCIS run or one splat, repeated once (the second run is the warm one)."""
+    import torch
+    from . import scenes
+    from .build import build
+    from .sim import Simulator, mcis, render
+
+    build()
+    out = {}
+    for rep in range(2):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if args.mcis:
+            case = scenes.mcis_case()
+            torch.cuda.synchronize()
+            e0.record()
+            r = mcis(case["surf_off"], case["surf"], case["cand_off"], case["cand"], case["draw_off"], case["u"])
+            e1.record()
+            torch.cuda.synchronize()
+            out = {"what": "mcis", "candidates": int(case["cand_off"][-1]), "ms": e0.elapsed_time(e1),
+                   "picked_valid": bool((r["picked"] >= 0).all().item())}
+        else:
+            sc = scenes.WORKLOADS[args.workload]()
+            s = Simulator.from_scene(sc)
+            v, C, F = scenes.key_frames(sc, 1, k_seed=81, fs=0.05)[0]
+            s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+            s.load_covariance(scenes.gaussian_covariances(sc))
+            cov = s.covariance()
+            col, op = scenes.gaussian_appearance(sc)
+            dev = torch.device("cuda")
+            mean = torch.as_tensor(sc.x, device=dev)
+            W, H = 1024, 768
+            view, fx, fy, cx, cy = scenes.camera(W, H)
+            torch.cuda.synchronize()
+            e0.record()
+            img, T = render(mean, cov, torch.as_tensor(col, device=dev), torch.as_tensor(op, device=dev), view,
+                            fx, fy, cx, cy, W, H)
+            e1.record()
+            torch.cuda.synchronize()
+            s.close()
+            out = {"what": "render", "gaussians": sc.n, "ms": e0.elapsed_time(e1),
+                   "coverage": float((T < 0.5).float().mean().item())}
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":
