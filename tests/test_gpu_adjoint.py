@@ -200,6 +200,9 @@ def test_backward_argument_errors(sim_mod):
     with pytest.raises(L.MpmError):
         s.step(1, record=True)
     s.close()
+    for bad in (-1, 2):                                              # tape_grid is 0 or 1
+        with pytest.raises(L.MpmError):
+            sim_mod.Simulator.from_scene(sc, tape_grid=bad)
 
 
 def test_grid_tape_overflow_reruns_with_whole_pool_slots(orc, sim_mod):
