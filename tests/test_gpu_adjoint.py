@@ -256,3 +256,71 @@ def test_grid_tape_overflow_reruns_with_whole_pool_slots(orc, sim_mod):
     for j in range(2):
         assert np.abs(g_ref[:, j]).max() > 0
         assert rel(g[:, j], g_ref[:, j]) < GRAD_TOL, (j, rel(g[:, j], g_ref[:, j]))
+
+
+def test_reverse_pass_without_graphs_matches_graph_replay(sim_mod):
+    """The reverse pass launched directly (the recompute of the previous
+    segment forked onto the side stream with events, no captured graphs)
+    gives the gradients of the graph-replayed reverse pass, for both tape
+    modes: 40 substeps of the 512-particle ball, checkpoint every 10 (four
+    segments), frames at 20 and 40, from a stressed seeded start."""
+    sc = scenes.ball_512()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=66, vs=0.1, cs=1.0, fs=0.02)[0]
+    dev = torch.device("cuda")
+    init = {"x": torch.as_tensor(sc.x, device=dev), "v": torch.as_tensor(v, device=dev),
+            "C": torch.as_tensor(C, device=dev), "F": torch.as_tensor(F, device=dev),
+            "vol": torch.as_tensor(sc.vol, device=dev), "mat_id": torch.as_tensor(sc.mat_id, device=dev)}
+    target = init["x"][None] + 0.002
+    out = {}
+    for tape_grid in (0, 1):
+        for use_graph in (True, False):
+            s = sim_mod.Simulator.from_scene(sc, ckpt_every=10, tape_grid=tape_grid)
+            s.set_tuning(1, 128, use_graph)
+            p = torch.as_tensor(sc.params, device=dev).clone().requires_grad_(True)
+            xs = sim_mod.trajectory(p, s, init, [20, 40])
+            (g,) = torch.autograd.grad(((xs - target) ** 2).sum(), p)
+            s.sync()
+            out[(tape_grid, use_graph)] = g.double().cpu().numpy()
+            s.close()
+    ref = out[(0, True)]
+    assert np.abs(ref[:, 0]).max() > 0
+    for k, g in out.items():
+        for j in range(2):
+            assert rel(g[:, j], ref[:, j]) < GRAD_TOL, (k, j, rel(g[:, j], ref[:, j]))
+
+
+@pytest.mark.parametrize("tape_grid", [0, 1])
+def test_fwd_bwd_captured_in_one_cuda_graph_both_tape_modes(sim_mod, tape_grid):
+    """A whole fwd+bwd of the 512-particle ball (40 substeps, checkpoint
+    every 10) captured by the caller with torch.cuda.graph, for both tape
+    modes, replayed twice: the gradients of the run outside the capture."""
+    sc = scenes.ball_512()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=67, vs=0.1, cs=1.0, fs=0.02)[0]
+    dev = torch.device("cuda")
+    init = {"x": torch.as_tensor(sc.x, device=dev), "v": torch.as_tensor(v, device=dev),
+            "C": torch.as_tensor(C, device=dev), "F": torch.as_tensor(F, device=dev),
+            "vol": torch.as_tensor(sc.vol, device=dev), "mat_id": torch.as_tensor(sc.mat_id, device=dev)}
+    target = init["x"][None] + 0.002
+    s = sim_mod.Simulator.from_scene(sc, ckpt_every=10, tape_grid=tape_grid)
+    p = torch.as_tensor(sc.params, device=dev).clone().requires_grad_(True)
+
+    def fb():
+        xs = sim_mod.trajectory(p, s, init, [20, 40])
+        (g,) = torch.autograd.grad(((xs - target) ** 2).sum(), p)
+        return g
+
+    ref = fb().double().cpu().numpy()
+    fb()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        out = fb()
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        r = out.double().cpu().numpy()
+        for j in range(2):
+            assert rel(r[:, j], ref[:, j]) < GRAD_TOL, (j, rel(r[:, j], ref[:, j]))
+    s.sync()
+    assert s.stats()["device_error"] == 0
+    s.close()
