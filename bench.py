@@ -63,6 +63,17 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+def load_peak_clock_mhz():
+    """Maximum SM clock: from MEASURED_PEAKS.json, else the GB300's 2070 MHz."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        if d.get("sm_max_mhz"):
+            return float(d["sm_max_mhz"])
+    return 2070.0
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -258,7 +269,7 @@ def run_ours(args):
     achieved = FWD_BYTES_PER_PS * n / avg_fused_s / 1e9
     # DRAM bytes per launch from the committed ncu capture, only while the
     # kernel sources are the ones that capture measured
-    traffic = None
+    traffic = inst = None
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         from paper_2602_01723_gb300.profiling import source_hash
@@ -266,6 +277,17 @@ def run_ours(args):
             t = json.load(f).get("k_substep_fused_three_objects_300k")
         if t and t.get("source_hash") == source_hash() and t.get("particles") == n:
             traffic = t["bytes_per_launch"]
+            inst = t.get("warp_instructions_per_launch")
+    # the same kernel against the issue ceiling: warp instructions per launch
+    # (same capture) over the launch time, against one instruction per cycle
+    # per scheduler (4 per SM) at the maximum SM clock
+    issue = None
+    if traffic is not None and inst:
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        peak_issue = sms * 4 * load_peak_clock_mhz() * 1e6
+        issue = {"warp_instructions_per_launch": inst, "achieved": inst / avg_fused_s, "peak": peak_issue,
+                 "unit": "warp instructions/s", "frac": inst / avg_fused_s / peak_issue,
+                 "peak_kind": "SMs x 4 schedulers x maximum SM clock"}
 
     # end to end through the C ABI with host (pinned) buffers
     xh = torch.as_tensor(sc.x).pin_memory()
@@ -334,7 +356,7 @@ def run_ours(args):
                          "launches": fused_n, "bytes_per_particle_substep": FWD_BYTES_PER_PS,
                          "peak_kind": peak_kind,
                          "timing": "CUDA events around each launch on the launching stream, over a second pass "
-                                   "of the timed steps"},
+                                   "of the timed steps", "issue": issue},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d substeps of the %d-particle scene, FP64 oracle, 1 thread, %.1f s"
                                        % (ORACLE_SAMPLE_SUBSTEPS, n, cpu_t)},

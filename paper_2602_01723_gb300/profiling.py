@@ -99,7 +99,7 @@ def kernel(rep, out_md, cmd, traffic_key=None, particles=None):
     hdr, units = rows[0], rows[1]
     idx = {h: i for i, h in enumerate(hdr)}
     lines = ["# Kernel profile", "", "Command:", "", "```", cmd, "```", ""]
-    per_launch = []
+    per_launch, inst = [], []
     for r in rows[2:]:
         name = r[idx["Kernel Name"]] if "Kernel Name" in idx else "?"
         lines += ["## `%s`" % name, "", "| metric | value | unit |", "|---|---|---|"]
@@ -120,6 +120,8 @@ def kernel(rep, out_md, cmd, traffic_key=None, particles=None):
         rd = _bytes(r[idx["dram__bytes_read.sum"]], units[idx["dram__bytes_read.sum"]])
         wr = _bytes(r[idx["dram__bytes_write.sum"]], units[idx["dram__bytes_write.sum"]])
         per_launch.append(rd + wr)
+        if "smsp__inst_executed.sum" in idx:
+            inst.append(float(r[idx["smsp__inst_executed.sum"]].replace(",", "")))
     with open(out_md, "w") as f:
         f.write("\n".join(lines) + "\n")
     if traffic_key and per_launch:
@@ -131,6 +133,8 @@ def kernel(rep, out_md, cmd, traffic_key=None, particles=None):
         d[traffic_key] = {"bytes_per_launch": b, "source_hash": source_hash(), "launches": len(per_launch),
                           "particles": particles, "note": "dram__bytes_read.sum + dram__bytes_write.sum, "
                           "ncu --set full (cold L2 per replay)", "hashed_sources": list(KERNEL_SOURCES)}
+        if inst:
+            d[traffic_key]["warp_instructions_per_launch"] = sum(inst) / len(inst)
         with open(TRAFFIC, "w") as f:
             json.dump(d, f, indent=1)
 
