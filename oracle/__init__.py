@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the MLS-MPM substep and its adjoint (ctypes wrapper).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  The product path
+CPU-baseline and reference legs of ``bench.py`` may import this package.  The product path
 (``paper_2602_01723_gb300``) never imports it and shares no code with it.
 
 The arithmetic lives in ``mpm_oracle.c`` (plain C, double precision, scalar

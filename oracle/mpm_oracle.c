@@ -41,6 +41,12 @@
  *
  * The SVD here is cyclic Jacobi on F^T F; the CUDA path uses a different,
  * closed-form method.  Results are compared only on invariant quantities.
+ *
+ * Parity unpinned: the free-running trajectory over many substeps (orc_run).
+ * The paper prints no trajectory to check it against.  Its pins are those
+ * of each step (conservation of mass and momentum, free fall, a rigid
+ * rotation carried exactly, the stress and return-map identities) and the
+ * central differences of its own adjoint.
  */
 #include <math.h>
 #include <stdlib.h>
