@@ -45,6 +45,14 @@ __global__ void k_load(Dev D, const float *__restrict__ x, const float *__restri
             c[i] = C ? C[9 * p + i] : 0.f;
             f[i] = F ? F[9 * p + i] : ((i % 4 == 0) ? 1.f : 0.f);
         }
+        // every input the substep reads must be finite: a NaN would otherwise be
+        // dropped silently by the fixed-point scatter instead of reported
+        bool fin = isfinite(x[3 * p]) && isfinite(x[3 * p + 1]) && isfinite(x[3 * p + 2]) && isfinite(vp) &&
+                   isfinite(mu) && isfinite(lam) && isfinite(ys);
+        if (v) fin = fin && isfinite(v[3 * p]) && isfinite(v[3 * p + 1]) && isfinite(v[3 * p + 2]);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fin = fin && isfinite(c[i]) && isfinite(f[i]);
+        if (!fin) set_err(D, ERRB_NONFINITE);
         int info = T.elastic[m] | (T.plastic[m] << 4) | (m << 8);
         float4 *r = D.rec + (size_t)p * REC_F4;
         r[0] = make_float4(x[3 * p], x[3 * p + 1], x[3 * p + 2], T.rho[m] * vp);

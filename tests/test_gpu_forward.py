@@ -189,6 +189,47 @@ def test_leaving_the_domain_mid_run_reports_error(sim_mod):
     s.close()
 
 
+@pytest.mark.parametrize("field", ["v", "C", "F", "vol"])
+def test_non_finite_input_reports_error_until_reload(sim_mod, field):
+    """A NaN in any input the substep reads is reported by the load
+    (MPM_ERR_NONFINITE): the fixed-point scatter would otherwise turn it into
+    zero momentum without a trace.  The context then refuses to step until a
+    valid load clears it."""
+    from paper_2602_01723_gb300 import _lib as L
+    sc = scenes.cube_8k()
+    arrays = {"v": np.zeros((sc.n, 3), np.float32), "C": np.zeros((sc.n, 9), np.float32),
+              "F": np.tile(np.eye(3, dtype=np.float32).reshape(1, 9), (sc.n, 1)), "vol": sc.vol.copy()}
+    arrays[field].reshape(sc.n, -1)[5, 0] = np.nan
+    s = sim_mod.Simulator.from_scene(sc)
+    with pytest.raises(L.MpmError) as e:
+        s.load(sc.x, arrays["vol"], sc.mat_id, v=arrays["v"], C=arrays["C"], F=arrays["F"])
+    assert e.value.status == 5, (e.value.status, str(e.value))
+    with pytest.raises(L.MpmError) as e2:
+        s.step(1)
+    assert e2.value.status == 7                                 # MPM_ERR_STATE until reloaded
+    s.load_scene(sc)
+    s.step(3)
+    s.sync()
+    s.close()
+
+
+def test_neo_hookean_inverted_element_reports_non_finite(sim_mod):
+    """Neo-Hookean stress needs log J: a particle with det F < 0 is an
+    error (MPM_ERR_NONFINITE), not clamped."""
+    from paper_2602_01723_gb300 import _lib as L
+    sc = scenes.cube_8k()
+    mats = [scenes.material(1, 0, 1e4, 0.3, 1.0)]
+    F = np.tile(np.eye(3, dtype=np.float32).reshape(1, 9), (sc.n, 1))
+    F[11, 0] = -1.0
+    s = sim_mod.Simulator(sc.grid_res, sc.dx, sc.dt, sc.gravity, mats)
+    s.load(sc.x, sc.vol, np.zeros(sc.n, np.int32), F=F)
+    s.step(2)
+    with pytest.raises(L.MpmError) as e:
+        s.sync()
+    assert e.value.status == 5, (e.value.status, str(e.value))
+    s.close()
+
+
 def test_three_objects_full_size(orc, sim_mod):
     """The 300k-particle, 128^3 three-object scene at full size, in the
     launch configuration bench.py times, from a stressed seeded key frame
