@@ -82,3 +82,37 @@ def test_noalloc_rejects_oversize_grids_before_any_device_work(L):
     st = lib.mpm_substep_noalloc((ctypes.c_int32 * 3)(32, 32, 32), 1 / 32, 1e-4, (ctypes.c_float * 3)(0, -9.8, 0),
                                  mats, 17, None, 1, p, p, p, p, p, p, p, p, p, p, None)
     assert st == 1                                # more than 16 materials
+
+
+def test_binding_struct_layouts_match_the_header(L, tmp_path):
+    """The ctypes mirrors of mpm_material, mpm_options and mpm_bgdo_options
+    have the size and field offsets that a C compiler gives the header's
+    declarations (a C program built with gcc prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = {"mpm_material": L.mpm_material, "mpm_options": L.mpm_options,
+               "mpm_bgdo_options": L.mpm_bgdo_options}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mpm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append('printf("%s sizeof %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s %s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True,
+                   capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in out:
+        if line:
+            a, b, c = line.split()
+            got[(a, b)] = int(c)
+    for name, cls in structs.items():
+        assert got[(name, "sizeof")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
