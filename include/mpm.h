@@ -97,11 +97,16 @@ typedef struct {
     int32_t scatter;            /* P2G scatter: 0 shared-memory float atomics, 1 int32 fixed-point
                                    shared-memory atomics (default), 2 direct global reductions */
     int32_t tape_grid;          /* reverse pass: 0 (default) keeps, for every state of a checkpoint
-                                   segment, the binning and grid that the segment's recompute built,
-                                   so that a reverse substep runs only its adjoint kernels (device
-                                   memory per state: about 2 KB per grid-pool block plus 12 B per
-                                   particle); 1 rebuilds them in every reverse substep.  0 falls back
-                                   to 1 when that memory cannot be allocated. */
+                                   segment, the records, binning and grid that the segment's
+                                   recompute built, so that a reverse substep runs only its adjoint
+                                   kernels; two banks of ckpt_every states, so that the recompute
+                                   of the next segment overlaps the reverse of this one.  Device
+                                   memory per state: 132 B per particle, 8 B per grid block, and
+                                   2 KB per block of a grid pool sized at twice the active blocks
+                                   (grown to the whole pool, and the pass rerun, if a state
+                                   outgrows it).  1 keeps one bank of records only and rebuilds
+                                   binning and grid in every reverse substep.  0 falls back to 1
+                                   when its memory cannot be allocated. */
     int32_t reserved[6];
 } mpm_options;
 
