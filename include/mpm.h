@@ -357,18 +357,25 @@ MPM_API mpm_status mpm_debug_p2g(mpm_ctx *ctx, float *m, float *mv, void *stream
  * work overlaps (different streams, or different host threads on one device)
  * race on the scratch: serialise them.
  *
- * The first call on a device looks up the scratch's device address for that
- * device (host code cannot use the array's symbol directly); make that first
- * call before any stream capture.
+ * Set-up: the first call on a device, with that device current, looks up
+ * the scratch's device address for that device (host code cannot use the
+ * array's symbol directly) and keeps it for the life of the process; make
+ * that first call before any stream capture begins.  The kept address is not
+ * looked up again, so do not call this entry point after cudaDeviceReset.
  *
  * Arguments: grid_res, dx, dt, gravity, table, n_materials as in mpm_create
- * (table on the host); opt (nullable) supplies bound and walls.  x, v (n x 3),
- * C, F (n x 9), vol (n), material_id (n) are device arrays; the outputs x_out,
- * v_out (n x 3), C_out, F_out (n x 9) are device arrays and may alias the
- * inputs.  Per-particle parameters come from the table only.  Synchronises
- * the stream; returns MPM_ERR_OUT_OF_DOMAIN when a particle's stencil leaves
- * the grid or a material id is out of range, MPM_ERR_NONFINITE on a
- * non-finite result, MPM_ERR_INVALID_ARG for NULL or host pointers.
+ * (table on the host), checked as mpm_create checks them (nu in (-1, 0.5),
+ * E, rho > 0) but with elastic models 0..1 and plastic models 0..2 only;
+ * opt (nullable) supplies bound (>= 0) and walls (MPM_WALL_*).  x, v (n x 3),
+ * C, F (n x 9), vol (n), material_id (n) are arrays on the current device;
+ * the outputs x_out, v_out (n x 3), C_out, F_out (n x 9) are arrays on the
+ * current device and may alias the inputs.  Per-particle parameters come from
+ * the table only.  Every argument is checked before any GPU work:
+ * MPM_ERR_INVALID_ARG for a bad argument, a NULL or host pointer or one on
+ * another device, MPM_ERR_CAPACITY for a grid beyond the scratch.  Each call
+ * synchronises the stream before it returns, to read the error word: then
+ * MPM_ERR_OUT_OF_DOMAIN when a particle's stencil leaves the grid or a
+ * material id is out of range, MPM_ERR_NONFINITE on a non-finite result.
  * ------------------------------------------------------------------------- */
 #define MPM_NOALLOC_MAX_NODES 262144      /* 64^3 */
 #define MPM_NOALLOC_MAX_MATERIALS 16

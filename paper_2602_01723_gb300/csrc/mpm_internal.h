@@ -8,6 +8,7 @@
 
 #include "../../include/mpm.h"
 #include "mpm_dev.cuh"
+#include "mpm_ptr.h"
 
 namespace mpm {
 

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "../../include/mpm.h"
+#include "mpm_ptr.h"
 #include "mpm_scan.cuh"
 
 namespace {
@@ -266,12 +267,7 @@ __global__ void k_mc_draw(int n_obj, const int64_t *coff, const int64_t *doff, c
     }
 }
 
-bool is_dev(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool is_dev(const void *p) { return mpm::on_this_device(p); }
 
 int blocks_for(long long n, int t) {
     long long b = (n + t - 1) / t;
@@ -298,6 +294,10 @@ extern "C" MPM_API mpm_status mpm_mcis(int32_t n_obj, const int64_t *surf_off, c
         }
     if (surf_off[0] != 0 || cand_off[0] != 0 || draw_off[0] != 0) {
         g_mcis_msg = "mcis: offsets must start at 0";
+        return MPM_ERR_INVALID_ARG;
+    }
+    if (mpm::any_on_other_device({surf, cand, u, d, w, picked})) {
+        g_mcis_msg = "mcis: an array lives on another device than the current one";
         return MPM_ERR_INVALID_ARG;
     }
     const long long ns = surf_off[n_obj], nc = cand_off[n_obj], nd = draw_off[n_obj];

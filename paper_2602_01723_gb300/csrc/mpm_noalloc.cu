@@ -23,6 +23,7 @@
 #include "../../include/mpm.h"
 #include "mpm_dev.cuh"
 #include "mpm_math.cuh"
+#include "mpm_ptr.h"
 
 namespace {
 
@@ -201,15 +202,6 @@ __global__ void k_na_g2p(Params P, const float4 *grid, unsigned *err, const floa
     for (int t = 0; t < 9; ++t) { C_out[9 * p + t] = Cn[t]; F_out[9 * p + t] = G[t]; }
 }
 
-bool device_accessible(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 }  // namespace
 
 extern "C" MPM_API mpm_status mpm_substep_noalloc(const int32_t grid_res[3], float dx, float dt, const float gravity[3],
@@ -221,9 +213,24 @@ extern "C" MPM_API mpm_status mpm_substep_noalloc(const int32_t grid_res[3], flo
     if (!grid_res || !gravity || !table || !x || !v || !C || !F || !vol || !material_id || !x_out || !v_out ||
         !C_out || !F_out)
         return MPM_ERR_INVALID_ARG;
-    if (n < 1 || n > (1ll << 31) - 1 || !(dx > 0.f) || !(dt > 0.f) || n_materials < 1 ||
-        n_materials > MAX_MATERIALS)
+    if (n < 1 || n > (1ll << 31) - 1 || !(dx > 0.f) || !(dt > 0.f) || !std::isfinite(dx) || !std::isfinite(dt) ||
+        n_materials < 1 || n_materials > MAX_MATERIALS)
         return MPM_ERR_INVALID_ARG;
+    // the checks mpm_create makes on the same arguments, then the scratch
+    // capacity, then the arrays: all before any GPU work
+    mpm_options o;
+    mpm_default_options(&o);
+    if (opt) o = *opt;
+    if (o.bound < 0) return MPM_ERR_INVALID_ARG;
+    for (int i = 0; i < 6; ++i)
+        if (o.walls[i] < MPM_WALL_OPEN || o.walls[i] > MPM_WALL_STICKY) return MPM_ERR_INVALID_ARG;
+    for (int m = 0; m < n_materials; ++m) {
+        const mpm_material &t = table[m];
+        if (t.elastic < 0 || t.elastic > 1 || t.plastic < 0 || t.plastic > 2 || !(t.E > 0.f) || !(t.rho > 0.f) ||
+            !(t.nu > -1.f && t.nu < 0.5f) || !std::isfinite(t.E) || !std::isfinite(t.rho) ||
+            !std::isfinite(t.yield_stress) || !std::isfinite(t.friction_angle_deg))
+            return MPM_ERR_INVALID_ARG;
+    }
     long long nodes = 1;
     for (int d = 0; d < 3; ++d) {
         if (grid_res[d] < 4) return MPM_ERR_INVALID_ARG;
@@ -232,10 +239,7 @@ extern "C" MPM_API mpm_status mpm_substep_noalloc(const int32_t grid_res[3], flo
     if (nodes > MAX_NODES) return MPM_ERR_CAPACITY;   // the scratch grid holds at most MAX_NODES nodes
     const void *arrays[] = {x, v, C, F, vol, material_id, x_out, v_out, C_out, F_out};
     for (const void *a : arrays)
-        if (!device_accessible(a)) return MPM_ERR_INVALID_ARG;
-    mpm_options o;
-    mpm_default_options(&o);
-    if (opt) o = *opt;
+        if (!on_this_device(a)) return MPM_ERR_INVALID_ARG;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) { cudaGetLastError(); return MPM_ERR_CUDA; }
@@ -265,8 +269,6 @@ extern "C" MPM_API mpm_status mpm_substep_noalloc(const int32_t grid_res[3], flo
     P.n_mat = n_materials;
     for (int m = 0; m < n_materials; ++m) {
         const mpm_material &t = table[m];
-        if (t.elastic < 0 || t.elastic > 1 || t.plastic < 0 || t.plastic > 2 || !(t.E > 0.f) || !(t.rho > 0.f))
-            return MPM_ERR_INVALID_ARG;
         P.E[m] = t.E; P.nu[m] = t.nu; P.rho[m] = t.rho; P.yield[m] = t.yield_stress;
         P.elastic[m] = t.elastic; P.plastic[m] = t.plastic;
         const double sphi = std::sin(t.friction_angle_deg * M_PI / 180.0);

@@ -24,6 +24,7 @@
 #include <string>
 
 #include "../../include/mpm.h"
+#include "mpm_ptr.h"
 #include "mpm_scan.cuh"
 
 namespace {
@@ -218,12 +219,7 @@ __global__ void __launch_bounds__(TS * TS) k_rd_blend(Cam c, const uint2 *ranges
     }
 }
 
-bool is_dev(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool is_dev(const void *p) { return mpm::on_this_device(p); }
 
 
 int blocks_for(long long n, int t) {
@@ -243,6 +239,10 @@ extern "C" MPM_API mpm_status mpm_render(int64_t n, const float *mean, const flo
     if (n < 0 || (n > 0 && (!mean || !cov || !color || !opacity)) || !view || !bg || !image || width < 1 ||
         height < 1 || width > 16384 || height > 16384 || n >= (1ll << 31)) {
         g_render_msg = "render: bad arguments";
+        return MPM_ERR_INVALID_ARG;
+    }
+    if (mpm::any_on_other_device({mean, cov, color, opacity, image, trans})) {
+        g_render_msg = "render: an array lives on another device than the current one";
         return MPM_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;

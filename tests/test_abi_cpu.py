@@ -84,6 +84,40 @@ def test_noalloc_rejects_oversize_grids_before_any_device_work(L):
     assert st == 1                                # more than 16 materials
 
 
+@pytest.mark.parametrize("case", ["nu_half", "nu_minus_one", "negative_bound", "wall_code", "elastic_model",
+                                  "plastic_model", "nonfinite_E"])
+def test_noalloc_checks_the_table_and_options_like_mpm_create(L, case):
+    """The allocation-free entry point rejects, as mpm_create does, a table or
+    options that mpm_create rejects, and does so before anything else: on a
+    grid too large for its scratch it still answers MPM_ERR_INVALID_ARG, not
+    MPM_ERR_CAPACITY."""
+    lib = L.lib()
+    h = np.zeros(64, dtype=np.float32)
+    p = ctypes.c_void_p(h.ctypes.data)
+    m = dict(elastic=0, plastic=0, E=1e4, nu=0.3, rho=1.0, ys=0.0, phi=30.0)
+    opt = L.mpm_default_options()
+    if case == "nu_half":
+        m["nu"] = 0.5
+    elif case == "nu_minus_one":
+        m["nu"] = -1.0
+    elif case == "negative_bound":
+        opt.bound = -1
+    elif case == "wall_code":
+        opt.walls[3] = 3
+    elif case == "elastic_model":
+        m["elastic"] = 2                          # the further models run through mpm_create only
+    elif case == "plastic_model":
+        m["plastic"] = 3
+    elif case == "nonfinite_E":
+        m["E"] = float("inf")
+    mats = (L.mpm_material * 1)(L.mpm_material(m["elastic"], m["plastic"], m["E"], m["nu"], m["rho"], m["ys"],
+                                               m["phi"]))
+    big = (ctypes.c_int32 * 3)(128, 128, 32)
+    st = lib.mpm_substep_noalloc(big, 1 / 128, 1e-4, (ctypes.c_float * 3)(0, -9.8, 0), mats, 1, ctypes.byref(opt), 1,
+                                 p, p, p, p, p, p, p, p, p, p, None)
+    assert st == 1, (case, st)                    # MPM_ERR_INVALID_ARG before the capacity check
+
+
 def test_binding_struct_layouts_match_the_header(L, tmp_path):
     """The ctypes mirrors of mpm_material, mpm_options and mpm_bgdo_options
     have the size and field offsets that a C compiler gives the header's

@@ -125,3 +125,23 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     st, _ = _noalloc(sc, {"x": sc.x, "v": v, "C": C, "F": F}, res=(128, 128, 32))
     assert st == 8   # MPM_ERR_CAPACITY: 128*128*32 nodes > MPM_NOALLOC_MAX_NODES
     assert L.STATUS_NAMES[st] == "MPM_ERR_CAPACITY"
+
+
+def test_noalloc_error_word_does_not_leak_into_the_next_call():
+    """The scratch's error word is shared by every call, like its grid.  A
+    first call with one particle outside the grid (x = 0.01, whose stencil
+    would start at node -1) returns MPM_ERR_OUT_OF_DOMAIN; the next call, with
+    the valid seeded state on the same stream, returns MPM_OK and matches the
+    oracle: each call clears the error word before it runs."""
+    from __graft_entry__ import build
+    build()
+    sc, v, C, F = _scene()
+    bad_x = sc.x.copy()
+    bad_x[5] = [0.01, 0.5, 0.5]
+    st, _ = _noalloc(sc, {"x": bad_x, "v": v, "C": C, "F": F})
+    assert st == 4                                    # MPM_ERR_OUT_OF_DOMAIN
+    s0 = {"x": sc.x, "v": v, "C": C, "F": F}
+    st, n1 = _noalloc(sc, s0)
+    assert st == 0
+    e_ref = _errors(n1, _oracle_step(sc, s0), sc)
+    assert all(e < t for e, t in zip(e_ref, TOL)), e_ref
