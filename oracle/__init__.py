@@ -86,7 +86,8 @@ def lib():
             L.orc_backward.argtypes = [cp, ctypes.c_long, mp, ctypes.c_int, _P, ctypes.c_int, _PI, _P, _P, _P]
             L.orc_covariance.argtypes = [ctypes.c_long, _P, _P, _P]
             L.orc_render.argtypes = [ctypes.c_long, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                     ctypes.c_double, _P]
             _PL = ctypes.POINTER(ctypes.c_long)
             L.orc_mcis.argtypes = [ctypes.c_int, _PL, _P, _PL, _P, _PL, _P, ctypes.c_double, ctypes.c_double, _P, _P,
                                    ctypes.POINTER(ctypes.c_longlong), _PL]
@@ -418,15 +419,20 @@ def mcis(surf_off, surf, cand_off, cand, draw_off, u, sigma=0.02, eps=1e-6):
     return {"d": d, "w": w, "cum": cum, "picked": picked}
 
 
-def render(mean, cov, col, opac, view, fx, fy, cx, cy, W, H, bg=(0.0, 0.0, 0.0)):
+def render(mean, cov, col, opac, view, fx, fy, cx, cy, W, H, bg=(0.0, 0.0, 0.0), tie_eps=None):
     """Splat the Gaussians (§3.1) into an H x W x 3 image; view is the 3x4
-    [R | T] world-to-camera transform.  Returns (image, transmittance)."""
+    [R | T] world-to-camera transform.  Returns (image, transmittance), and
+    with tie_eps also the per-pixel order-ambiguity bound: how far reordering
+    layers whose depths agree within tie_eps times the magnitude of their
+    depth's terms (or drawing or dropping one that near the near plane) can
+    move the pixel's colour."""
     mean = _f64(mean, (-1, 3))
     n = len(mean)
     cv, cl, op = _f64(cov, (n, 6)), _f64(col, (n, 3)), _f64(opac, (n,))
     vw, b = _f64(view, (12,)), _f64(bg, (3,))
     img = np.zeros((H, W, 3))
     T = np.zeros((H, W))
+    amb = np.zeros((H, W)) if tie_eps is not None else None
     lib().orc_render(n, _d(mean), _d(cv), _d(cl), _d(op), _d(vw), float(fx), float(fy), float(cx), float(cy), int(W),
-                     int(H), _d(b), _d(img), _d(T))
-    return img, T
+                     int(H), _d(b), _d(img), _d(T), float(tie_eps or 0.0), _d(amb) if amb is not None else None)
+    return (img, T) if amb is None else (img, T, amb)

@@ -1235,14 +1235,25 @@ void orc_mcis(int n_obj, const long *surf_off, const double *surf, const long *c
 /*     1/255; a pixel stops when its transmittance would drop below 1e-4;   */
 /*   - the background is added with the remaining transmittance;            */
 /*   - order: by t_z, ties by index.                                         */
-/* Brute force per pixel over all Gaussians, in double precision, except the */
-/* depth that orders the Gaussians and decides the near-plane test: that is */
-/* a decision the kernel takes in FP32, so it is taken here in FP32 too,     */
-/* from the FP32 view and positions, one rounded operation at a time in the */
-/* kernel's order.                                                           */
+/* Brute force per pixel over all Gaussians, in double precision.            */
+/*                                                                          */
+/* Order ambiguity (optional output amb, per pixel).  An implementation that */
+/* computes t_z in lower precision may order two Gaussians whose depths lie  */
+/* within its rounding the other way, and may draw or drop a Gaussian whose  */
+/* t_z lies within its rounding of 0.2.  Gaussian i's depth is given the     */
+/* error bound delta_i = tie_eps (|R_20 mu_0| + |R_21 mu_1| + |R_22 mu_2| +  */
+/* |T_2|).  Swapping two layers that follow each other at a pixel, with      */
+/* transmittance T in front of them, changes the colour by                   */
+/*     T alpha_1 alpha_2 (col_1 - col_2)                                     */
+/* and leaves the transmittance behind them unchanged (both orders leave     */
+/* T (1 - alpha_1)(1 - alpha_2)).  amb adds, per pixel, T alpha_1 alpha_2    */
+/* max_k |col_1k - col_2k| for every pair of consecutive contributing layers */
+/* whose depths differ by at most delta_1 + delta_2, and T alpha for every   */
+/* Gaussian within its delta of the near plane (drawn or not): a bound on    */
+/* how far any such reordering can move the pixel.                          */
 /* ------------------------------------------------------------------------ */
 
-typedef struct { double u, v, ca, cb, cc, depth; int rx0, rx1, ry0, ry1, ok; } orc_splat;
+typedef struct { double u, v, ca, cb, cc, depth, delta; int rx0, rx1, ry0, ry1, ok, maybe; } orc_splat;
 
 static int splat_cmp_depth(const void *a, const void *b) {
     const double *x = (const double *)a, *y = (const double *)b;
@@ -1253,7 +1264,7 @@ static int splat_cmp_depth(const void *a, const void *b) {
 
 void orc_render(long n, const double *mean, const double *cov, const double *col, const double *opac,
                 const double *view, double fx, double fy, double cx, double cy, int W, int H, const double *bg,
-                double *img, double *T_out) {
+                double *img, double *T_out, double tie_eps, double *amb) {
     const int TS = 16;
     const int gx = (W + TS - 1) / TS, gy = (H + TS - 1) / TS;
     orc_splat *sp = (orc_splat *)malloc((n > 0 ? n : 1) * sizeof(orc_splat));
@@ -1263,10 +1274,11 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
         const double *R = view, *p = mean + 3 * i;
         double t[3];
         for (int r = 0; r < 3; ++r) t[r] = R[4 * r] * p[0] + R[4 * r + 1] * p[1] + R[4 * r + 2] * p[2] + R[4 * r + 3];
-        const float zf = (((float)R[8] * (float)p[0] + (float)R[9] * (float)p[1]) + (float)R[10] * (float)p[2]) +
-                         (float)R[11];
+        const double delta = tie_eps * (fabs(R[8] * p[0]) + fabs(R[9] * p[1]) + fabs(R[10] * p[2]) + fabs(R[11]));
         sp[i].ok = 0;
-        if (!(zf > 0.2f)) continue;
+        /* drawn when t_z > 0.2; within delta of it, amb counts it either way */
+        const int maybe = amb && fabs(t[2] - 0.2) <= delta;
+        if (!(t[2] > 0.2) && !maybe) continue;
         const double *c = cov + 6 * i;
         double S[9] = {c[0], c[1], c[2], c[1], c[3], c[4], c[2], c[4], c[5]}, Wr[9], WS[9], Sc[9];
         for (int r = 0; r < 3; ++r)
@@ -1291,10 +1303,11 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
         int x0 = (int)fmin(gx, fmax(0.0, floor((u - rad) / TS))), x1 = (int)fmin(gx, fmax(0.0, floor((u + rad + TS - 1) / TS)));
         int y0 = (int)fmin(gy, fmax(0.0, floor((v - rad) / TS))), y1 = (int)fmin(gy, fmax(0.0, floor((v + rad + TS - 1) / TS)));
         if (x1 <= x0 || y1 <= y0) continue;
-        sp[i].u = u; sp[i].v = v; sp[i].depth = t[2];
+        sp[i].u = u; sp[i].v = v; sp[i].depth = t[2]; sp[i].delta = delta;
         sp[i].ca = d / det; sp[i].cb = -b / det; sp[i].cc = a / det;
         sp[i].rx0 = x0; sp[i].rx1 = x1; sp[i].ry0 = y0; sp[i].ry1 = y1; sp[i].ok = 1;
-        order[2 * m] = (double)zf;
+        sp[i].maybe = maybe;
+        order[2 * m] = t[2];
         order[2 * m + 1] = (double)i;
         ++m;
     }
@@ -1302,7 +1315,9 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
     for (int py = 0; py < H; ++py)
         for (int px = 0; px < W; ++px) {
             const int tx = px / TS, ty = py / TS;
-            double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0}, A = 0.0;
+            long prev = -1;                    /* previous contributing layer */
+            double prev_alpha = 0.0, prev_T = 1.0;
             for (long q = 0; q < m; ++q) {
                 const long i = (long)order[2 * q + 1];
                 const orc_splat *g = &sp[i];
@@ -1312,14 +1327,25 @@ void orc_render(long n, const double *mean, const double *cov, const double *col
                 if (power > 0.0) continue;
                 double alpha = fmin(0.99, opac[i] * exp(power));
                 if (alpha < 1.0 / 255.0) continue;
+                if (g->maybe) {
+                    A += T * alpha;
+                    if (!(g->depth > 0.2)) continue;       /* not drawn here */
+                }
                 const double tt = T * (1.0 - alpha);
                 if (tt < 1e-4) break;
+                if (amb && prev >= 0 && fabs(g->depth - sp[prev].depth) <= g->delta + sp[prev].delta) {
+                    double dc = 0.0;
+                    for (int k = 0; k < 3; ++k) dc = fmax(dc, fabs(col[3 * i + k] - col[3 * prev + k]));
+                    A += prev_T * prev_alpha * alpha * dc;
+                }
                 for (int k = 0; k < 3; ++k) C[k] += col[3 * i + k] * alpha * T;
+                prev = i; prev_alpha = alpha; prev_T = T;
                 T = tt;
             }
             double *o = img + 3 * ((size_t)py * W + px);
             for (int k = 0; k < 3; ++k) o[k] = C[k] + T * bg[k];
             if (T_out) T_out[(size_t)py * W + px] = T;
+            if (amb) amb[(size_t)py * W + px] = A;
         }
     free(sp);
     free(order);

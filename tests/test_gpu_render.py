@@ -1,7 +1,15 @@
 """GPU parity of the Gaussian splatting (§3.1) against the FP64 oracle on the
-same seeded Gaussians and camera.  Per pixel the FP32 compositing of up to a
-few hundred contributions stays within 2e-4; a threshold decision (alpha
-against 1/255, transmittance against 1e-4) that FP32 and FP64 take
+same seeded Gaussians and camera.
+
+The oracle orders the Gaussians by their FP64 camera depth.  The kernel takes
+that decision in FP32, so where two layers of a pixel have depths within the
+FP32 rounding of the depth, both orders are correct: the oracle returns, per
+pixel, the largest change such a swap (or drawing or dropping a Gaussian that
+close to the near plane) can make, T alpha_1 alpha_2 |col_1 - col_2|, with a
+depth error bound of 2^-21 times the magnitude of the depth's terms (about
+eight FP32 roundings).  Every pixel is held to 2e-4 (the FP32 compositing of
+up to a few hundred contributions) plus that bound.  A threshold decision
+(alpha against 1/255, transmittance against 1e-4) that FP32 and FP64 take
 differently changes a pixel by at most 1/255 of a colour, so at most a few
 pixels in a thousand may differ by up to 0.01."""
 import numpy as np
@@ -13,6 +21,7 @@ pytestmark = pytest.mark.gpu
 from paper_2602_01723_gb300 import scenes  # noqa: E402
 
 PIX_TOL, FLIP_TOL, FLIP_FRAC = 2e-4, 1e-2, 2e-3
+TIE_EPS = 2.0 ** -21
 
 
 @pytest.fixture(scope="module")
@@ -23,11 +32,16 @@ def sim_mod():
     return sim
 
 
-def compare(got, ref):
+def compare(got, ref, amb):
+    """Per pixel |got - ref| <= PIX_TOL + amb, except threshold flips."""
     err = np.abs(got - ref)
     per_pix = err.reshape(err.shape[0], err.shape[1], -1).max(axis=2)
-    assert per_pix.max() <= FLIP_TOL, per_pix.max()
-    assert (per_pix > PIX_TOL).mean() <= FLIP_FRAC, (per_pix > PIX_TOL).mean()
+    excess = per_pix - amb
+    assert excess.max() <= FLIP_TOL, excess.max()
+    assert (excess > PIX_TOL).mean() <= FLIP_FRAC, (excess > PIX_TOL).mean()
+    used = (per_pix > PIX_TOL) & (excess <= PIX_TOL)
+    return "%d pixels with an order ambiguity (largest bound %.3g, median %.3g), %d of them beyond 2e-4" % (
+        int((amb > 0).sum()), amb.max(), np.median(amb[amb > 0]) if (amb > 0).any() else 0.0, int(used.sum()))
 
 
 def scene_gaussians(sc, fs=0.1, k_seed=81):
@@ -46,7 +60,7 @@ def test_render_matches_the_oracle(orc, sim_mod, host):
     cov = orc.covariance(F, cov0).astype(np.float32)
     view, fx, fy, cx, cy = scenes.camera(120, 90, eye=(0.5, 0.5, -0.3), target=(0.5, 0.5, 0.5))
     bg = (0.1, 0.2, 0.3)
-    ref, Tref = orc.render(sc.x, cov, col, op, view, fx, fy, cx, cy, 120, 90, bg)
+    ref, Tref, amb = orc.render(sc.x, cov, col, op, view, fx, fy, cx, cy, 120, 90, bg, tie_eps=TIE_EPS)
     if host:
         import ctypes
         from paper_2602_01723_gb300 import _lib as L
@@ -59,9 +73,10 @@ def test_render_matches_the_oracle(orc, sim_mod, host):
     else:
         img, T = sim_mod.render(sc.x, cov, col, op, view, fx, fy, cx, cy, 120, 90, bg)
         img, T = img.cpu().numpy(), T.cpu().numpy()
-    compare(img, ref)
-    compare(T[..., None], Tref[..., None])
+    n_amb = compare(img, ref, amb)
+    compare(T[..., None], Tref[..., None], np.zeros_like(amb))    # a swap leaves the transmittance unchanged
     assert (Tref < 0.5).mean() > 0.05      # the objects cover part of the image
+    print("render 120 x 90: %s" % n_amb)
 
 
 def test_render_transparent_and_empty(orc, sim_mod):
@@ -88,6 +103,7 @@ def test_render_full_size_300k(orc, sim_mod):
     img, T = sim_mod.render(sc.x, cov, col, op, view, fx, fy, cx, cy, W, H)
     img = img.cpu().numpy()
     for (x0, y0) in [(464, 400), (224, 448)]:
-        ref, _ = orc.render(sc.x, cov, col, op, view, fx, fy, cx - x0, cy - y0, 64, 64)
-        compare(img[y0:y0 + 64, x0:x0 + 64], ref)
+        ref, _, amb = orc.render(sc.x, cov, col, op, view, fx, fy, cx - x0, cy - y0, 64, 64, tie_eps=TIE_EPS)
+        n_amb = compare(img[y0:y0 + 64, x0:x0 + 64], ref, amb)
         assert ref.max() > 0.1
+        print("render crop (%d, %d): %s" % (x0, y0, n_amb))

@@ -88,3 +88,45 @@ def test_transmittance_cut_off():
                            31.5, 31.5, W, W)
     np.testing.assert_allclose(img[31, 31], [0.99, 0.99 * 0.01, 0.0], atol=1e-14)
     assert abs(T[31, 31] - 1e-4) < 1e-15
+
+
+def test_order_ambiguity_bound_is_the_swap_of_two_layers():
+    """Two Gaussians at exactly the same camera depth on one ray: ties keep
+    the input order, so giving them in both orders composites both orders.
+    The two images differ by alpha_1 alpha_2 (col_1 - col_2) per channel in
+    front of full transmittance, the transmittance is the same, and the
+    ambiguity bound at that pixel is the largest channel of that difference."""
+    mean = [[0.5, 0.5, 0.5], [0.5, 0.5, 0.5]]
+    col = [[1.0, 0.2, 0.0], [0.0, 0.6, 0.3]]
+    op = [0.6, 0.5]
+    cov = [iso(1e-4), iso(2e-4)]
+    bg = (0.1, 0.1, 0.1)
+    a, Ta, amb = oracle.render(mean, cov, col, op, VIEW, F, F, 31.5, 31.5, W, W, bg, tie_eps=2.0 ** -21)
+    b, Tb, _ = oracle.render(mean[::-1], cov[::-1], col[::-1], op[::-1], VIEW, F, F, 31.5, 31.5, W, W, bg,
+                             tie_eps=2.0 ** -21)
+    a1, a2 = 0.6, 0.5                       # both centred on pixel (31, 31)
+    np.testing.assert_allclose(a[31, 31] - b[31, 31], a1 * a2 * (np.array(col[0]) - np.array(col[1])), atol=1e-14)
+    np.testing.assert_allclose(Ta, Tb, atol=1e-15)
+    assert abs(amb[31, 31] - a1 * a2 * 1.0) < 1e-14
+    # wherever the two orders differ, the bound covers the difference
+    diff = np.abs(a - b).max(axis=2)
+    assert np.all(diff <= amb + 1e-14) and amb.max() > 0
+    # without a tolerance the bound is off and the image is unchanged
+    c, _ = oracle.render(mean, cov, col, op, VIEW, F, F, 31.5, 31.5, W, W, bg)
+    np.testing.assert_array_equal(a, c)
+
+
+def test_order_ambiguity_bound_at_the_near_plane():
+    """A Gaussian whose camera depth is the near plane itself (0.2) may be
+    drawn or not by an implementation that rounds its depth: the bound at
+    its centre is its alpha in front of full transmittance; distinct depths
+    far apart give no bound."""
+    near = [[0.5, 0.5, -1.8]]               # camera depth exactly 0.2
+    img, T, amb = oracle.render(near, [iso(1e-6)], [[1.0, 1.0, 1.0]], [0.7], VIEW, F, F, 31.5, 31.5, W, W,
+                                tie_eps=2.0 ** -21)
+    assert np.all(T == 1.0)                 # t_z > 0.2 is false: not drawn
+    assert abs(amb[31, 31] - 0.7) < 1e-14
+    far = [[0.5, 0.5, 0.5], [0.5, 0.5, 0.1]]
+    _, _, amb2 = oracle.render(far, [iso(1e-4)] * 2, [[1, 0, 0], [0, 1, 0]], [0.6, 0.5], VIEW, F, F, 31.5, 31.5, W,
+                               W, tie_eps=2.0 ** -21)
+    assert np.all(amb2 == 0.0)
