@@ -369,12 +369,13 @@ __device__ void load_tile(const Dev &D, const float4 *src, unsigned ep, int inst
 }
 
 struct ParticleIn {
-    float x[3], v[3], C[9], F[9];
+    int q[3];                      // fixed-point position (cells = q 2^-qf)
+    float v[3], C[9], F[9];
     float mass, vol, mu, lam, yield, alpha;
     int elastic, plastic;
 };
 __device__ __forceinline__ void unpack_particle(const float4 r[REC_F4], ParticleIn &P) {
-    P.x[0] = r[0].x; P.x[1] = r[0].y; P.x[2] = r[0].z; P.mass = r[0].w;
+    P.q[0] = rec_q(r[0].x); P.q[1] = rec_q(r[0].y); P.q[2] = rec_q(r[0].z); P.mass = r[0].w;
     P.v[0] = r[1].x; P.v[1] = r[1].y; P.v[2] = r[1].z; P.vol = r[1].w;
     P.C[0] = r[2].x; P.C[1] = r[2].y; P.C[2] = r[2].z; P.C[3] = r[2].w;
     P.C[4] = r[3].x; P.C[5] = r[3].y; P.C[6] = r[3].z; P.C[7] = r[3].w; P.C[8] = r[4].x;
@@ -524,9 +525,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
             unpack_particle(rr, P);
             float f[3];
             int b[3];
-            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
-            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
-            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
+            b[0] = base_cell_q(P.q[0], D, f[0]) - bx * BLK;
+            b[1] = base_cell_q(P.q[1], D, f[1]) - by * BLK;
+            b[2] = base_cell_q(P.q[2], D, f[2]) - bz * BLK;
             const bool ok = (unsigned)b[0] <= 3u && (unsigned)b[1] <= 3u && (unsigned)b[2] <= 3u;
             if (!ok) { set_err(D, ERRB_CFL); b[0] = min(max(b[0], 0), 3); b[1] = min(max(b[1], 0), 3); b[2] = min(max(b[2], 0), 3); }
             float w[3][3], dw[3][3];
@@ -832,17 +833,17 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout,
             unpack_particle(rr, P);
             float f[3];
             int b[3];
-            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
-            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
-            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
+            b[0] = base_cell_q(P.q[0], D, f[0]) - bx * BLK;
+            b[1] = base_cell_q(P.q[1], D, f[1]) - by * BLK;
+            b[2] = base_cell_q(P.q[2], D, f[2]) - bz * BLK;
             if ((unsigned)b[0] > 3u || (unsigned)b[1] > 3u || (unsigned)b[2] > 3u) { set_err(D, ERRB_CFL); ok = false; }
         }
         if (ok) {
             float f[3];
             int b[3];
-            b[0] = base_cell(P.x[0], inv_dx, f[0]) - bx * BLK;
-            b[1] = base_cell(P.x[1], inv_dx, f[1]) - by * BLK;
-            b[2] = base_cell(P.x[2], inv_dx, f[2]) - bz * BLK;
+            b[0] = base_cell_q(P.q[0], D, f[0]) - bx * BLK;
+            b[1] = base_cell_q(P.q[1], D, f[1]) - by * BLK;
+            b[2] = base_cell_q(P.q[2], D, f[2]) - bz * BLK;
             float w[3][3], dw[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
@@ -1510,6 +1511,8 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
     if (S <= 0) return ctx_fail(ctx, MPM_ERR_STATE, "nothing recorded: call mpm_step with record != 0 first");
     if (n_frames < 0 || (n_frames > 0 && (!frame_substep || !dL_dx)) || !dL_dparams)
         return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "bad frames / gradient arguments");
+    if (any_on_other_device({dL_dx, dL_dparams, dL_dstate0}))
+        return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     for (int f = 0; f < n_frames; ++f)
         if (frame_substep[f] < 0 || frame_substep[f] > S)
             return ctx_fail(ctx, MPM_ERR_INVALID_ARG, "frame_substep outside [0, recorded substeps]");

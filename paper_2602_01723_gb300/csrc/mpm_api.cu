@@ -4,6 +4,7 @@
 // device error word to mpm_status.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdint>
@@ -69,15 +70,7 @@ template <typename T> void dfree(T *&p) {
 
 }  // namespace
 
-bool mpm::is_device_ptr(const void *p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
+bool mpm::is_device_ptr(const void *p) { return on_this_device(p); }
 
 bool mpm::stream_capturing(cudaStream_t st) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -397,6 +390,9 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     D.n_inst = o.n_instances;
     ctx->dx = dx; ctx->dt = dt;
     D.dx = dx; D.inv_dx = 1.f / dx; D.dt = dt;
+    D.qf = position_fraction_bits(std::max(grid_res[0], std::max(grid_res[1], grid_res[2])));
+    D.q_cell = std::ldexp(1.f, D.qf);
+    D.q_unit = std::ldexp(1.f, -D.qf);
     D.bound = o.bound;
     for (int i = 0; i < 6; ++i) D.wall[i] = o.walls[i];
     ctx->opt = o;
@@ -473,6 +469,8 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (n <= 0 || n > (1ll << 31) - 1 || !x || !vol || !material_id)
         return fail(ctx, MPM_ERR_INVALID_ARG, "n must be in [1, 2^31) and x, vol, material_id non-NULL");
+    if (any_on_other_device({x, v, C, F, vol, material_id, instance, params}))
+        return fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     cudaStream_t st = S(stream);
     const bool cap = stream_capturing(st);
     if (cap && (n > ctx->cap || !ctx->D.rec))
@@ -527,6 +525,7 @@ MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, vo
 MPM_API mpm_status mpm_get_particles(mpm_ctx *ctx, float *x, float *v, float *C, float *F, void *stream) {
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    if (any_on_other_device({x, v, C, F})) return fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     cudaStream_t st = S(stream);
     Dev &D = ctx->D;
     size_t n = (size_t)D.n;
@@ -754,6 +753,7 @@ MPM_API mpm_status mpm_bgdo(mpm_ctx *ctx, int32_t n_keys, const int32_t *slots, 
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (n_keys < 1 || n_keys > MPM_MAX_SNAPSHOTS || !slots)
         return fail(ctx, MPM_ERR_INVALID_ARG, "n_keys must be in [1, MPM_MAX_SNAPSHOTS] with a slot list");
+    if (any_on_other_device({G, log_E, g_tau, delta})) return fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     mpm_bgdo_options o;
     mpm_bgdo_default_options(&o);
     if (opt) o = *opt;
@@ -842,6 +842,7 @@ MPM_API mpm_status mpm_bgdo(mpm_ctx *ctx, int32_t n_keys, const int32_t *slots, 
 MPM_API mpm_status mpm_load_covariance(mpm_ctx *ctx, const float *cov0, void *stream) {
     if (!ctx || !cov0) return MPM_ERR_INVALID_ARG;
     if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    if (any_on_other_device({cov0})) return fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     const size_t n = (size_t)ctx->D.n;
     mpm_status s;
     if (ctx->cov_cap < ctx->cap) {
@@ -856,6 +857,7 @@ MPM_API mpm_status mpm_load_covariance(mpm_ctx *ctx, const float *cov0, void *st
 MPM_API mpm_status mpm_get_covariance(mpm_ctx *ctx, float *cov, void *stream) {
     if (!ctx || !cov) return MPM_ERR_INVALID_ARG;
     if (!ctx->loaded) return fail(ctx, MPM_ERR_STATE, "no particles loaded");
+    if (any_on_other_device({cov})) return fail(ctx, MPM_ERR_INVALID_ARG, "an array lives on another device than the current one");
     if (!ctx->cov0 || ctx->cov_n != ctx->D.n)
         return fail(ctx, MPM_ERR_STATE, "no rest covariances loaded for this particle count");
     cudaStream_t st = S(stream);

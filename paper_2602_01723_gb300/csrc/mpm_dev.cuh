@@ -8,13 +8,35 @@ namespace mpm {
 
 // One particle = one 128-byte record (8 x float4), stored in the caller's
 // order and never permuted; kernels reach particles through the sorted index.
-//   f4[0] = x0 x1 x2 mass        f4[1] = v0 v1 v2 vol
+//   f4[0] = q0 q1 q2 mass        f4[1] = v0 v1 v2 vol
 //   f4[2] = C0 C1 C2 C3          f4[3] = C4 C5 C6 C7
 //   f4[4] = C8 F0 F1 F2          f4[5] = F3 F4 F5 F6
 //   f4[6] = F7 F8 mu lambda      f4[7] = yield info instance alpha
 // (alpha: Drucker-Prager coefficient of the friction angle; nu = lambda / (2 (lambda + mu)))
 // info bits: elastic model [0,4), plastic model [4,8), material id [8,32).
+//
+// Positions q0 q1 q2 are int32 bit patterns: signed fixed point in grid-cell
+// units, x_d = q_d 2^-qf dx, with qf fraction bits per context (Dev::qf).
+// Every cell then has the same resolution, 2^-qf of a cell, where an FP32
+// world coordinate loses precision away from the origin: at 256 nodes per
+// axis (qf = 22) a position resolves 2.4e-7 of a cell everywhere, against
+// 1.5e-5 of a cell for an FP32 coordinate near the middle of the domain.  That
+// FP32 rounding, taken once per substep by x += dt v, would otherwise bound
+// the trajectory's agreement with an exact integrator.  The base node and the
+// spline fraction of a position follow exactly from integer arithmetic
+// (base_cell_q).
 constexpr int REC_F4 = 8;
+
+// fraction bits of the fixed-point position for a grid of at most r_max
+// nodes per axis: the largest |q| (twice the grid, leaving room for particles
+// that leave it) fits in int32, and qf <= 23 keeps the spline fraction's
+// numerator below 2^24, so that it converts to float exactly
+inline int position_fraction_bits(int r_max) {
+    int lg = 0;
+    while ((1 << lg) < 2 * r_max) ++lg;
+    const int qf = 31 - lg;
+    return qf < 23 ? qf : 23;
+}
 
 // The grid is block-sparse: 4x4x4-node blocks, a dense page table per grid
 // buffer (block key -> pool slot), an epoch tag per entry telling whether the
@@ -39,6 +61,9 @@ struct Dev {
     int bpi;               // blocks per instance
     int n_inst;
     float dx, inv_dx, dt;
+    int qf;                // fraction bits of the fixed-point positions
+    float q_cell;          // 2^qf: fixed-point units per cell
+    float q_unit;          // 2^-qf: cells per fixed-point unit
     float g[3];
     int bound;
     int wall[6];
@@ -102,6 +127,27 @@ __device__ __forceinline__ int base_cell(float x, float inv_dx, float &fx) {
     fx = X - b;
     return (int)b;
 }
+
+// the same for a fixed-point position q (cells = q 2^-qf): b = floor(X - 1/2)
+// by an arithmetic shift, fx = X - b in [0.5, 1.5) exactly (the numerator
+// q - b 2^qf stays below 1.5 2^qf <= 1.5 2^23)
+__device__ __forceinline__ int base_cell_q(int q, const Dev &D, float &fx) {
+    const int b = (q - (1 << (D.qf - 1))) >> D.qf;
+    fx = (float)(q - (b << D.qf)) * D.q_unit;
+    return b;
+}
+
+// fixed-point position after a displacement of dt v: the displacement in
+// cells is rounded once to the fixed-point grid; the sum saturates in int32
+// (a particle that far out is reported as out of the domain)
+__device__ __forceinline__ int advance_q(int q, float v, const Dev &D) {
+    float dq = D.dt * v * D.inv_dx * D.q_cell;
+    dq = fminf(fmaxf(dq, -1.0e9f), 1.0e9f);          // NaN becomes a bound too
+    const long long s = (long long)q + (long long)__float2ll_rn(dq);
+    return (int)(s < -2147483647ll ? -2147483647ll : (s > 2147483647ll ? 2147483647ll : s));
+}
+
+__device__ __forceinline__ int rec_q(float f) { return __float_as_int(f); }
 
 __device__ __forceinline__ void set_err(const Dev &D, unsigned bit) { atomicOr(D.err, bit); }
 

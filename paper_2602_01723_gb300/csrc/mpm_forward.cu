@@ -49,13 +49,23 @@ __global__ void k_load(Dev D, const float *__restrict__ x, const float *__restri
         // dropped silently by the fixed-point scatter instead of reported
         bool fin = isfinite(x[3 * p]) && isfinite(x[3 * p + 1]) && isfinite(x[3 * p + 2]) && isfinite(vp) &&
                    isfinite(mu) && isfinite(lam) && isfinite(ys);
+        // fixed-point position: cells = x / dx, rounded to 2^-qf of a cell
+        // (exact for FP32 inputs away from the origin); beyond +-2^30 units it
+        // saturates, and the binning reports the particle as out of the domain
+        int q[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double u = (double)x[3 * p + d] / (double)D.dx * (double)D.q_cell;
+            u = isfinite(u) ? fmin(fmax(u, -1073741824.0), 1073741824.0) : 0.0;
+            q[d] = (int)llrint(u);
+        }
         if (v) fin = fin && isfinite(v[3 * p]) && isfinite(v[3 * p + 1]) && isfinite(v[3 * p + 2]);
 #pragma unroll
         for (int i = 0; i < 9; ++i) fin = fin && isfinite(c[i]) && isfinite(f[i]);
         if (!fin) set_err(D, ERRB_NONFINITE);
         int info = T.elastic[m] | (T.plastic[m] << 4) | (m << 8);
         float4 *r = D.rec + (size_t)p * REC_F4;
-        r[0] = make_float4(x[3 * p], x[3 * p + 1], x[3 * p + 2], T.rho[m] * vp);
+        r[0] = make_float4(__int_as_float(q[0]), __int_as_float(q[1]), __int_as_float(q[2]), T.rho[m] * vp);
         r[1] = v ? make_float4(v[3 * p], v[3 * p + 1], v[3 * p + 2], vp) : make_float4(0.f, 0.f, 0.f, vp);
         r[2] = make_float4(c[0], c[1], c[2], c[3]);
         r[3] = make_float4(c[4], c[5], c[6], c[7]);
@@ -70,10 +80,11 @@ __global__ void k_load(Dev D, const float *__restrict__ x, const float *__restri
 // binning helpers
 // ---------------------------------------------------------------------------
 
-// Particle block key from its position; false when the stencil leaves the grid.
-__device__ __forceinline__ bool particle_key(const Dev &D, float x0, float x1, float x2, int inst, unsigned &key) {
+// Particle block key from its fixed-point position; false when the stencil
+// leaves the grid.
+__device__ __forceinline__ bool particle_key(const Dev &D, int q0, int q1, int q2, int inst, unsigned &key) {
     float f;
-    int b0 = base_cell(x0, D.inv_dx, f), b1 = base_cell(x1, D.inv_dx, f), b2 = base_cell(x2, D.inv_dx, f);
+    int b0 = base_cell_q(q0, D, f), b1 = base_cell_q(q1, D, f), b2 = base_cell_q(q2, D, f);
     bool ok = b0 >= 0 && b1 >= 0 && b2 >= 0 && b0 <= D.R[0] - 3 && b1 <= D.R[1] - 3 && b2 <= D.R[2] - 3;
     if (!ok) {   // keep the index in range; the error bit makes the result void
         b0 = min(max(b0, 0), D.R[0] - 3);
@@ -124,7 +135,7 @@ __global__ void k_bin(Dev D) {
         float4 r0 = D.rec[(size_t)p * REC_F4];
         int inst = __float_as_int(D.rec[(size_t)p * REC_F4 + 7].z);
         unsigned key;
-        if (!particle_key(D, r0.x, r0.y, r0.z, inst, key)) set_err(D, ERRB_DOMAIN);
+        if (!particle_key(D, rec_q(r0.x), rec_q(r0.y), rec_q(r0.z), inst, key)) set_err(D, ERRB_DOMAIN);
         bin_particle(D, mask, (unsigned)p, key);
     }
 }
@@ -501,7 +512,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
             const float4 *nr = S.rec + j * RS_F4;
             float4 *sr = S.pk + j * PK_F4;
             const float4 r0 = nr[0], r1 = nr[1], r6 = nr[6], r7 = nr[7];
-            float x[3] = {r0.x, r0.y, r0.z};
+            int q[3] = {rec_q(r0.x), rec_q(r0.y), rec_q(r0.z)};
             const float mass = r0.w, vol = r1.w;
             float v[3] = {r1.x, r1.y, r1.z};
             const float mu = r6.z, lam = r6.w, yield = r7.x;
@@ -520,8 +531,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
             BinTicket ticket;
             if (GATHER) {
                 float f0, f1, f2;
-                int b0 = base_cell(x[0], inv_dx, f0) - ox, b1 = base_cell(x[1], inv_dx, f1) - oy,
-                    b2 = base_cell(x[2], inv_dx, f2) - oz;
+                int b0 = base_cell_q(q[0], D, f0) - ox, b1 = base_cell_q(q[1], D, f1) - oy,
+                    b2 = base_cell_q(q[2], D, f2) - oz;
                 if ((unsigned)b0 > 3u || (unsigned)b1 > 3u || (unsigned)b2 > 3u) {   // grouping invariant broken
                     set_err(D, ERRB_CFL);
                     b0 = min(max(b0, 0), 3); b1 = min(max(b1, 0), 3); b2 = min(max(b2, 0), 3);
@@ -566,8 +577,9 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
 #pragma unroll
                 for (int t = 0; t < 9; ++t) Cm[t] = cs * Bm[t];
 #pragma unroll
-                for (int d = 0; d < 3; ++d) { v[d] = vn[d]; x[d] += dt * vn[d]; }
-                in_dom = particle_key(D, x[0], x[1], x[2], inst, key);
+                for (int d = 0; d < 3; ++d) { v[d] = vn[d]; q[d] = advance_q(q[d], vn[d], D); }
+                if (!(isfinite(vn[0]) && isfinite(vn[1]) && isfinite(vn[2]))) set_err(D, ERRB_NONFINITE);
+                in_dom = particle_key(D, q[0], q[1], q[2], inst, key);
                 ticket = bin_begin(D, lane_mask, key);      // result consumed after the SVD
                 rp[1] = make_float4(v[0], v[1], v[2], vol);
                 rp[2] = make_float4(Cm[0], Cm[1], Cm[2], Cm[3]);
@@ -608,8 +620,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 }
 #pragma unroll
                 for (int t = 0; t < 9; ++t) F[t] = G[t];
-                if (!(isfinite(x[0]) && isfinite(x[1]) && isfinite(x[2]))) set_err(D, ERRB_NONFINITE);
-                rp[0] = make_float4(x[0], x[1], x[2], mass);
+                rp[0] = make_float4(__int_as_float(q[0]), __int_as_float(q[1]), __int_as_float(q[2]), mass);
                 rp[4] = make_float4(Cm[8], F[0], F[1], F[2]);
                 rp[5] = make_float4(F[3], F[4], F[5], F[6]);
                 rp[6] = make_float4(F[7], F[8], mu, lam);
@@ -627,7 +638,7 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 }
             }
 
-            if (!GATHER) in_dom = particle_key(D, x[0], x[1], x[2], inst, key);
+            if (!GATHER) in_dom = particle_key(D, q[0], q[1], q[2], inst, key);
             if (!in_dom) set_err(D, ERRB_DOMAIN);
 
             if (SCATTER) {
@@ -650,9 +661,11 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 Ad[6] = (mass * Cm[6] - kf * tau.xz) * dx; Ad[7] = (mass * Cm[7] - kf * tau.yz) * dx;
                 Ad[8] = (mass * Cm[8] - kf * tau.zz) * dx;
                 const float P0 = mass * v[0], P1 = mass * v[1], P2 = mass * v[2];
-                // tile-local continuous node coordinate of the new position
-                const float X0 = x[0] * inv_dx - (float)(ox - 1), X1 = x[1] * inv_dx - (float)(oy - 1),
-                            X2 = x[2] * inv_dx - (float)(oz - 1);
+                // tile-local continuous node coordinate of the new position (the
+                // integer offset is taken off in fixed point; one rounding)
+                const float X0 = (float)(q[0] - ((ox - 1) << D.qf)) * D.q_unit,
+                            X1 = (float)(q[1] - ((oy - 1) << D.qf)) * D.q_unit,
+                            X2 = (float)(q[2] - ((oz - 1) << D.qf)) * D.q_unit;
                 // base cell floor(X - 0.5) in [0, ST-3] keeps the 3^3 stencil in the tile
                 const bool in_tile = in_dom && X0 >= 0.5f && X1 >= 0.5f && X2 >= 0.5f && X0 < (float)ST - 1.5f &&
                                      X1 < (float)ST - 1.5f && X2 < (float)ST - 1.5f;
@@ -661,8 +674,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                     // moved out of the tile: straight to the global grid
                     pm = 0.f;
                     float f0, f1, f2;
-                    const int g0 = base_cell(x[0], inv_dx, f0), g1 = base_cell(x[1], inv_dx, f1),
-                              g2 = base_cell(x[2], inv_dx, f2);
+                    const int g0 = base_cell_q(q[0], D, f0), g1 = base_cell_q(q[1], D, f1),
+                              g2 = base_cell_q(q[2], D, f2);
                     float w0[3], w1[3], w2[3];
                     bspline_w(f0, w0);
                     bspline_w(f1, w1);
@@ -879,7 +892,13 @@ __global__ void k_export(Dev D, float *x, float *v, float *C, float *F) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < D.n; p += gridDim.x * blockDim.x) {
         const float4 *r = D.rec + (size_t)p * REC_F4;
         float4 r0 = r[0], r1 = r[1], r2 = r[2], r3 = r[3], r4 = r[4], r5 = r[5], r6 = r[6];
-        if (x) { x[3 * p] = r0.x; x[3 * p + 1] = r0.y; x[3 * p + 2] = r0.z; }
+        if (x) {
+            // fixed point -> world units, rounded once to FP32
+            const double u = (double)D.q_unit * (double)D.dx;
+            x[3 * p] = (float)(rec_q(r0.x) * u);
+            x[3 * p + 1] = (float)(rec_q(r0.y) * u);
+            x[3 * p + 2] = (float)(rec_q(r0.z) * u);
+        }
         if (v) { v[3 * p] = r1.x; v[3 * p + 1] = r1.y; v[3 * p + 2] = r1.z; }
         if (C) {
             float c[9] = {r2.x, r2.y, r2.z, r2.w, r3.x, r3.y, r3.z, r3.w, r4.x};

@@ -105,7 +105,10 @@ def test_one_substep_all_models(orc, sim_mod):
     got, ref = substep_compare(orc, sim_mod, sc, v, C, F)
     vs = np.abs(ref["v"]).max()
     assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * vs
-    assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
+    # x is returned as FP32 world coordinates: near 0.5 on this 32^3 grid one
+    # rounding of the output is up to 0.95e-6 dx by itself; the fixed-point
+    # state adds at most 2^-23 of a cell
+    assert np.abs(got["x"] - ref["x"]).max() < 2e-6 * sc.dx
     # C = 4/dx^2 sum w v_i (x_i - x_p)^T inherits the grid-velocity error: |dC| <= (6/dx) max|dv|
     assert np.abs(got["C"] - ref["C"]).max() < 6e-5 * np.abs(ref["v"]).max() / sc.dx
     # F after the return map: compare per particle relative to |F|
@@ -261,3 +264,59 @@ def test_three_objects_full_size(orc, sim_mod):
     st_ = s.stats()
     assert st_["device_error"] == 0
     s.close()
+
+
+def sheared_cube(plastic):
+    """The 8,192-particle cube driven by a smooth velocity field: simple
+    shear at rate 20/s plus (for sand) a uniform compression at 5/s, with the
+    matching affine field C = grad v, F = I, under gravity.  Over 100
+    substeps the accumulated shear strain (about 0.2) is far beyond the von
+    Mises yield strain sigma_y/(2 mu) = 0.0065 (sigma_y 50, E 1e4), so the
+    return map projects on every substep.  The sand is denser (rho 100), so
+    that its pressure waves are slow enough for it to stay compressed: its
+    particles sit on the cone and, as the compression relaxes, at the tip
+    (about a fifth of them by substep 100)."""
+    sc = scenes.cube_8k()
+    E, nu, rho = 1e4, 0.3, (100.0 if plastic == 2 else 10.0)
+    sc.materials = [scenes.material(0, plastic, E, nu, rho, yield_stress=50.0, friction_angle_deg=30.0)]
+    sc.mat_id = np.zeros(sc.n, np.int32)
+    s_rate, k_rate = 20.0, (5.0 if plastic == 2 else 0.0)
+    Gv = np.array([[-k_rate, s_rate, 0.0], [0.0, -k_rate, 0.0], [0.0, 0.0, -k_rate]])
+    v = ((sc.x.astype(np.float64) - 0.5) @ Gv.T).astype(np.float32)
+    C = np.tile(Gv.astype(np.float32), (sc.n, 1, 1))
+    return sc, v, C
+
+
+@pytest.mark.parametrize("plastic", [1, 2], ids=["von_mises", "drucker_prager"])
+def test_plastic_cube_free_running_100_substeps(orc, sim_mod, plastic):
+    """von Mises (App. A, eq. von_mises) and Drucker-Prager (eq. drucker_prager)
+    over 100 free-running substeps against the FP64 oracle: positions within
+    1e-4 dx and F within 1e-4 (the return map's FP32 projection of every
+    substep accumulates into F)."""
+    sc, v, C = sheared_cube(plastic)
+    got, ref = substep_compare(orc, sim_mod, sc, v, C, None, n_sub=100)
+    ex = np.abs(got["x"] - ref["x"]).max() / sc.dx
+    eF = np.abs(got["F"] - ref["F"]).max()
+    assert np.abs(ref["F"] - np.eye(3)).max() > 0.05                  # deformed well beyond yield
+    print("plastic %d, 100 substeps: x %.3g dx, F %.3g" % (plastic, ex, eF))
+    assert ex < POS_TOL_DX, ex
+    assert eF < 1e-4, eF
+
+
+def test_three_objects_full_size_30_substeps(orc, sim_mod):
+    """The 300k-particle, 128^3 three-object scene from its own start, in the
+    launch configuration bench.py times (graph replay of substep pairs):
+    positions after 30 free-running substeps within 1e-5 dx of the FP64
+    oracle, every particle."""
+    sc = scenes.three_objects_300k()
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(30)
+    s.sync()
+    got = to_np(s.get())
+    s.close()
+    cfg, mat = oracle_setup(orc, sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, 30)
+    ex = np.abs(got["x"] - ref["x"]).max() / sc.dx
+    print("three objects, 30 substeps: x %.3g dx" % ex)
+    assert ex < 1e-5, ex

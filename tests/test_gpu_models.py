@@ -3,7 +3,7 @@ StVK (Green strain), Hencky, fluid and volume elasticity, fluid and Sigma
 plasticity, against the FP64 oracle from the same seeded inputs: the P2G
 grid, one substep, a free-running run, the one-substep adjoint and BGDO.
 Tolerances as for the other models: grid 1e-5 relative, one-substep v and C
-1e-5 relative, x 1e-6 dx, F 2e-5, positions 1e-4 dx after 100 substeps,
+1e-5 relative, x 2e-6 dx (the FP32 output's own rounding is up to 0.95e-6 dx), F 2e-5, positions 1e-4 dx after 100 substeps,
 gradients 1e-3 relative."""
 import numpy as np
 import pytest
@@ -70,7 +70,7 @@ def test_one_substep_further_models(orc, sim_mod):
     # difference of large contributions, so the bound here is twice the
     # elastic-model one (1e-5)
     assert np.abs(got["v"] - ref["v"]).max() < 2e-5 * np.abs(ref["v"]).max()
-    assert np.abs(got["x"] - ref["x"]).max() < 1e-6 * sc.dx
+    assert np.abs(got["x"] - ref["x"]).max() < 2e-6 * sc.dx
     # C = 4/dx^2 sum w v_i (x_i - x_p)^T inherits the grid-velocity error: |dC| <= (6/dx) max|dv|
     assert np.abs(got["C"] - ref["C"]).max() < 6e-5 * np.abs(ref["v"]).max() / sc.dx
     assert np.abs(got["F"] - ref["F"]).max() < 2e-5

@@ -230,3 +230,112 @@ def test_batched_fwd_bwd_captured_in_one_cuda_graph(sim_mod):
         assert np.isfinite(r).all()
         assert np.abs(r - ref).max() < 1e-3 * np.abs(ref).max(), np.abs(r - ref).max() / np.abs(ref).max()
     s.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def _smallest_of_each_kind(sc):
+    """Instance ids of the smallest fixed-corotated, Neo-Hookean, plasticine
+    (von Mises) and sand (Drucker-Prager) instance of a batched scene.  The
+    plasticine one is the smallest whose yield strain sigma_y / (2 mu) is
+    below 0.05, so that it yields within the run and its yield-stress
+    gradient is not zero."""
+    counts = np.bincount(sc.instance, minlength=sc.n_instances)
+    kinds = {}
+    for b in np.argsort(counts, kind="stable"):
+        m = sc.materials[b]
+        k = ("nh" if m["elastic"] == 1 else "fcr") if m["plastic"] == 0 else ("vm" if m["plastic"] == 1 else "dp")
+        if k == "vm" and m["yield_stress"] / (m["E"] / (1.0 + m["nu"])) > 0.05:
+            continue
+        kinds.setdefault(k, int(b))
+    return kinds
+
+
+def test_batch_64_instances_match_the_oracle(orc, sim_mod):
+    """The 64-instance batch (1.47M particles, each instance on its own 64^3
+    grid) as one context: 200 substeps, recorded, then the reverse pass of
+    seeded cotangents at the ten frames (every 20 substeps) and the
+    per-instance reduction.  For the smallest instance of each material kind
+    the oracle runs that instance alone on its own grid (the instances are
+    independent problems, §4.2: one parameter set per instance label):
+    positions after 200 substeps within 1e-4 dx, per-particle gradients and
+    the per-instance sums within 1e-3 relative per parameter kind."""
+    sc = scenes.batch_64()
+    frames = [int(f) for f in sc.frame_sub]
+    cot = np.random.default_rng(64).standard_normal((len(frames), sc.n, 3)).astype(np.float32)
+    s = sim_mod.Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(sc.n_substeps, record=True)
+    x = s.positions().double().cpu().numpy()
+    g = s.backward(frames, torch.as_tensor(cot))
+    g_inst = s.reduce_by_material(g).double().cpu().numpy()
+    g = g.double().cpu().numpy()
+    assert s.stats()["device_error"] == 0
+    s.close()
+    for kind, b in sorted(_smallest_of_each_kind(sc).items()):
+        idx = np.nonzero(sc.instance == b)[0]
+        cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+        mat = orc.Material.from_table(sc.vol[idx], np.zeros(len(idx), np.int32), [sc.materials[b]])
+        _, tape = orc.run(cfg, orc.new_state(sc.x[idx], sc.v[idx]), mat, sc.n_substeps, tape=True)
+        ex = np.abs(x[idx] - tape[sc.n_substeps][:, 0:3]).max() / sc.dx
+        _, g_ref = orc.backward(cfg, mat, tape, frames, cot[:, idx].astype(np.float64))
+        kinds = [0, 1, 2] if kind == "vm" else [0, 1]
+        eg = [_rel(g[idx, j], g_ref[:, j]) for j in kinds]
+        es = [abs(g_inst[b, j] - g_ref[:, j].sum()) / np.abs(g_ref[:, j]).sum() for j in kinds]
+        print("instance %d (%s, %d particles): x %.3g dx, grads %s, sums %s"
+              % (b, kind, len(idx), ex, ["%.3g" % e for e in eg], ["%.3g" % e for e in es]))
+        assert ex < 1e-4, (kind, ex)
+        for j, e in zip(kinds, eg):
+            assert np.abs(g_ref[:, j]).max() > 0
+            assert e < 1e-3, (kind, j, e)
+        assert max(es) < 1e-3, (kind, es)
+
+
+def test_large_sparse_scene_on_the_256_grid_matches_the_oracle(orc, sim_mod):
+    """The 8-object large scene with 20,000 particles (2,500 per object) on
+    the full 256^3 block-sparse grid, dt 2e-5, checkpoint every 25: 100
+    substeps from a slightly stressed seeded start (so that the stress
+    gradient is physical before any contact), recorded, then the reverse pass
+    of seeded cotangents at substeps 25, 50, 75, 100 and the per-object
+    reduction by material id.  The plasticine objects' yield stress is
+    lowered to 100 (yield strain 0.013), so that they yield from the stressed
+    start and their yield-stress gradient is not zero.  The oracle holds the
+    256^3 grid densely in FP64.  Positions within 1e-4 dx; per-particle
+    gradients and per-object sums within 1e-3 relative per parameter kind."""
+    sc = scenes.large_2m(20_000)
+    for m in sc.materials:
+        if m["plastic"] == scenes.PLASTIC_VM:
+            m["yield_stress"] = 100.0
+    v, C, F = scenes.key_frames(sc, 1, k_seed=49, vs=0.1, cs=1.0, fs=0.02)[0]
+    params = np.stack([np.log([m["E"] for m in sc.materials]), [m["nu"] for m in sc.materials],
+                       [m["yield_stress"] for m in sc.materials]], axis=1)[sc.mat_id].astype(np.float32)
+    frames = [25, 50, 75, 100]
+    cot = np.random.default_rng(256).standard_normal((len(frames), sc.n, 3)).astype(np.float32)
+    s = sim_mod.Simulator.from_scene(sc)
+    assert s.grid_res == (256, 256, 256)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F, params=params)
+    s.step(100, record=True)
+    x = s.positions().double().cpu().numpy()
+    g = s.backward(frames, torch.as_tensor(cot))
+    g_obj = s.reduce_by_material(g).double().cpu().numpy()
+    g = g.double().cpu().numpy()
+    st = s.stats()
+    assert st["device_error"] == 0 and st["active_blocks"] < 0.01 * (256 // 4) ** 3, st
+    s.close()
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, params)
+    _, tape = orc.run(cfg, orc.new_state(sc.x, v, C, F), mat, 100, tape=True)
+    _, g_ref = orc.backward(cfg, mat, tape, frames, cot.astype(np.float64))
+    ex = np.abs(x - tape[100][:, 0:3]).max() / sc.dx
+    ref_obj = np.zeros((len(sc.materials), 3))
+    np.add.at(ref_obj, sc.mat_id, g_ref)
+    eg = [_rel(g[:, j], g_ref[:, j]) for j in range(3)]
+    eo = [_rel(g_obj[:, j], ref_obj[:, j]) for j in range(3)]
+    print("large scene 20k on 256^3: x %.3g dx, grads %s, per object %s"
+          % (ex, ["%.3g" % e for e in eg], ["%.3g" % e for e in eo]))
+    assert ex < 1e-4, ex
+    for j in range(3):
+        assert np.abs(g_ref[:, j]).max() > 0
+        assert eg[j] < 1e-3 and eo[j] < 1e-3, (j, eg[j], eo[j])
