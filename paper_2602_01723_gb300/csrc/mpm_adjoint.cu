@@ -345,6 +345,18 @@ __device__ __forceinline__ void lame_chain(float mu, float lam, float mubar, flo
 constexpr int GT = 6, GT3 = 216;
 constexpr int ADJ_THREADS = 128;
 
+// The reverse G2P and P2G kernels are specialised for the models a material
+// table uses, so that the common tables do not carry the registers, stack and
+// instruction footprint of the rarer models.  The reverse G2P (which reverses
+// the return map) by plasticity:
+//   ADJ_ELASTIC  none
+//   ADJ_PLASTIC  von Mises / Drucker-Prager
+//   ADJ_ALL      also fluid / Sigma plasticity
+// and the reverse P2G (which reverses the stress) by elasticity:
+//   ADJ_FCR      fixed-corotated only
+//   ADJ_FCR_NH   fixed-corotated and Neo-Hookean
+//   ADJ_ALL      also StVK, Hencky, fluid and volume elasticity
+
 __device__ __forceinline__ int page_slot_a(const Dev &D, int par, unsigned ep, int inst, int bx, int by, int bz) {
     if (bx < 0 || by < 0 || bz < 0 || bx >= D.NB[0] || by >= D.NB[1] || bz >= D.NB[2]) return -1;
     const unsigned k = block_key(D, inst, bx, by, bz);
@@ -474,6 +486,7 @@ __device__ __forceinline__ void adj_stage3(const Dev &D, AdjG2PSmem &S, int4 ch,
 // (x_i - x_p)) into an int32 fixed-point tile (per-chunk scale 2^30 / sum of
 // per-particle bounds) and flush it with one vector reduction per touched
 // node.
+template <int MS>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
                                                          float4 *gpar, float4 *gbar) {
     __shared__ AdjG2PSmem S;
@@ -533,15 +546,41 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
             float w[3][3], dw[3][3];
 #pragma unroll
             for (int a = 0; a < 3; ++a) { bspline_w(f[a], w[a]); bspline_dw(f[a], dw[a]); }
-            // recompute v' and C'
+            // adjoint of the new state
+            const float xb[3] = {aa[0].x, aa[0].y, aa[0].z};
+            const float vb[3] = {aa[0].w, aa[1].x, aa[1].y};
+            const float Cb[9] = {aa[1].z, aa[1].w, aa[2].x, aa[2].y, aa[2].z, aa[2].w, aa[3].x, aa[3].y, aa[3].z};
+            const float Fb[9] = {aa[3].w, aa[4].x, aa[4].y, aa[4].z, aa[4].w, aa[5].x, aa[5].y, aa[5].z, aa[5].w};
+            // x' = x + dt v': the velocity's total adjoint
+            float xa[3] = {xb[0], xb[1], xb[2]};
+            const float vt[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
+            // The reverse of the gathers v' = sum w v_i and C' = c4 sum w v_i (x_i - x_p)^T
+            // gives the position adjoint sum_i wbar_i grad w_i - c4 Ct^T sum_i w_i v_i,
+            // with wbar_i = vt . v_i + c4 v_i^T Ct (x_i - x_p) and Ct the total adjoint
+            // of C'.  The second term is c4 Ct^T v' (v' = sum w v_i), taken once after
+            // the node loop.  Without plasticity Ct = Cb + dt Fb F^T does not depend
+            // on C', so one pass over the 27 nodes recomputes v', C' and accumulates
+            // the first term; with plasticity Ct needs the return map of C', and a
+            // second pass follows.
+            float Ct[9];
             float vn[3] = {0.f, 0.f, 0.f}, Bm[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (MS == ADJ_ELASTIC) {
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 3; ++cc)
+                        Ct[3 * r + cc] = Cb[3 * r + cc] + dt * (Fb[3 * r] * P.F[3 * cc] + Fb[3 * r + 1] * P.F[3 * cc + 1] +
+                                                                 Fb[3 * r + 2] * P.F[3 * cc + 2]);
+            }
+            const float cdx = c4 * dx;
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const float wt = w[0][i] * w[1][jj] * w[2][k];
+                        const float wij = w[0][i] * w[1][jj];
+                        const float wt = wij * w[2][k];
                         const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
                         const float dd[3] = {(float)i - f[0], (float)jj - f[1], (float)k - f[2]};
                         const float a3[3] = {wt * g.x, wt * g.y, wt * g.z};
@@ -550,6 +589,17 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
                             vn[r] += a3[r];
 #pragma unroll
                             for (int cc = 0; cc < 3; ++cc) Bm[3 * r + cc] += a3[r] * dd[cc];
+                        }
+                        if (MS == ADJ_ELASTIC) {
+                            const float vi[3] = {g.x, g.y, g.z};
+                            float wbar = 0.f;
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                wbar += vi[r] * (vt[r] + cdx * (Ct[3 * r] * dd[0] + Ct[3 * r + 1] * dd[1] + Ct[3 * r + 2] * dd[2]));
+                            const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k], w[0][i] * dw[1][jj] * w[2][k],
+                                                 wij * dw[2][k]};
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) xa[cc] += wbar * inv_dx * gw[cc];
                         }
                     }
             float Cn[9], G[9];
@@ -561,19 +611,14 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
                 for (int cc = 0; cc < 3; ++cc)
                     G[3 * r + cc] = P.F[3 * r + cc] + dt * (Cn[3 * r] * P.F[cc] + Cn[3 * r + 1] * P.F[3 + cc] +
                                                             Cn[3 * r + 2] * P.F[6 + cc]);
-            // adjoint of the new state
-            const float xb[3] = {aa[0].x, aa[0].y, aa[0].z};
-            const float vb[3] = {aa[0].w, aa[1].x, aa[1].y};
-            const float Cb[9] = {aa[1].z, aa[1].w, aa[2].x, aa[2].y, aa[2].z, aa[2].w, aa[3].x, aa[3].y, aa[3].z};
-            const float Fb[9] = {aa[3].w, aa[4].x, aa[4].y, aa[4].z, aa[4].w, aa[5].x, aa[5].y, aa[5].z, aa[5].w};
             // reverse of the return map
             float Gb[9];
 #pragma unroll
             for (int t = 0; t < 9; ++t) Gb[t] = Fb[t];
             float mubar = 0.f, lambar = 0.f, ybar = 0.f;
-            if (P.plastic >= PLASTIC_FLUID) {
+            if (MS == ADJ_ALL && P.plastic >= PLASTIC_FLUID) {
                 volume_plastic_adjoint(P.plastic, G, Fb, Gb);
-            } else if (P.plastic != PLASTIC_NONE) {
+            } else if (MS != ADJ_ELASTIC && P.plastic != PLASTIC_NONE) {
                 float U[9], V[9], s3[3], e3[3], d3[3], z[3], ze[3];
                 svd3_robust(G, U, V, s3, e3, d3);
                 const int rm = return_map(P.plastic, s3, e3, d3, P.mu, P.lam, P.yield, P.alpha, z, ze);
@@ -582,43 +627,47 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
                                     lambar, ybar);
             }
             // G = (I + dt C') F
-            float Ct[9], Fp[9];
+            float Fp[9];
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
                 for (int cc = 0; cc < 3; ++cc) {
-                    Ct[3 * r + cc] = Cb[3 * r + cc] + dt * (Gb[3 * r] * P.F[3 * cc] + Gb[3 * r + 1] * P.F[3 * cc + 1] +
-                                                             Gb[3 * r + 2] * P.F[3 * cc + 2]);
+                    if (MS != ADJ_ELASTIC)
+                        Ct[3 * r + cc] = Cb[3 * r + cc] + dt * (Gb[3 * r] * P.F[3 * cc] + Gb[3 * r + 1] * P.F[3 * cc + 1] +
+                                                                 Gb[3 * r + 2] * P.F[3 * cc + 2]);
                     Fp[3 * r + cc] = Gb[3 * r + cc] + dt * (Cn[r] * Gb[cc] + Cn[3 + r] * Gb[3 + cc] + Cn[6 + r] * Gb[6 + cc]);
                 }
-            // x' = x + dt v'
-            float xa[3] = {xb[0], xb[1], xb[2]};
-            const float vt[3] = {vb[0] + dt * xb[0], vb[1] + dt * xb[1], vb[2] + dt * xb[2]};
-            // reverse of the gathers: position adjoint through the weights and x_i - x_p
+            if (MS != ADJ_ELASTIC) {
+                // second pass: the weights' term with the Ct of the return map's
+                // reverse (the outer loop stays rolled; its weights are selected,
+                // not indexed, so that they stay in registers)
 #pragma unroll 1
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i) {
+                    const float wi = i == 0 ? w[0][0] : (i == 1 ? w[0][1] : w[0][2]);
+                    const float dwi = i == 0 ? dw[0][0] : (i == 1 ? dw[0][1] : dw[0][2]);
+                    const float di = (float)i - f[0];
+                    const float4 *gi = S.g + (b[0] + i) * GT * GT;
 #pragma unroll
-                for (int jj = 0; jj < 3; ++jj)
+                    for (int jj = 0; jj < 3; ++jj)
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) {
-                        const float wt = w[0][i] * w[1][jj] * w[2][k];
-                        const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
-                                             w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
-                        const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
-                        const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
-                        const float vi[3] = {g.x, g.y, g.z};
-                        float wbar = 0.f;
+                        for (int k = 0; k < 3; ++k) {
+                            const float4 g = gi[(b[1] + jj) * GT + (b[2] + k)];
+                            const float dd[3] = {di, (float)jj - f[1], (float)k - f[2]};
+                            const float vi[3] = {g.x, g.y, g.z};
+                            float wbar = 0.f;
 #pragma unroll
-                        for (int r = 0; r < 3; ++r) {
-                            const float cd = Ct[3 * r] * dp[0] + Ct[3 * r + 1] * dp[1] + Ct[3 * r + 2] * dp[2];
-                            wbar += vt[r] * vi[r] + c4 * vi[r] * cd;
+                            for (int r = 0; r < 3; ++r)
+                                wbar += vi[r] * (vt[r] + cdx * (Ct[3 * r] * dd[0] + Ct[3 * r + 1] * dd[1] + Ct[3 * r + 2] * dd[2]));
+                            const float gw[3] = {dwi * w[1][jj] * w[2][k], wi * dw[1][jj] * w[2][k],
+                                                 wi * w[1][jj] * dw[2][k]};
+#pragma unroll
+                            for (int cc = 0; cc < 3; ++cc) xa[cc] += wbar * inv_dx * gw[cc];
                         }
+                }
+            }
+            // - c4 Ct^T v'
 #pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            const float dpb = c4 * wt * (Ct[cc] * vi[0] + Ct[3 + cc] * vi[1] + Ct[6 + cc] * vi[2]);
-                            xa[cc] += wbar * gw[cc] - dpb;
-                        }
-                    }
+            for (int cc = 0; cc < 3; ++cc) xa[cc] -= c4 * (Ct[cc] * vn[0] + Ct[3 + cc] * vn[1] + Ct[6 + cc] * vn[2]);
             float4 *op = aout + (size_t)p * ADJ_F4;
             op[0] = make_float4(xa[0], xa[1], xa[2], 0.f);
             op[1] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -788,6 +837,7 @@ __device__ __forceinline__ void adj_p2g_stage3(const Dev &D, AdjP2GSmem &S, int4
 }
 
 // three CTAs per SM (168 registers, a few bytes of spill) measured faster than two at 216
+template <int EL>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
     __shared__ AdjP2GSmem S;
     const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
@@ -850,8 +900,15 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout,
             // recompute the stress and the affine momentum A = m C - k tau
             float U[9], V[9], s3[3], e3[3], d3[3];
             Sym tau;
-            if (elastic_needs_svd(P.elastic)) svd3_robust(P.F, U, V, s3, e3, d3);
-            if (!kirchhoff(P.elastic, P.F, U, s3, e3, P.mu, P.lam, tau)) tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (EL == ADJ_ALL) {
+                if (elastic_needs_svd(P.elastic)) svd3_robust(P.F, U, V, s3, e3, d3);
+                if (!kirchhoff(P.elastic, P.F, U, s3, e3, P.mu, P.lam, tau)) tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            } else if (EL == ADJ_FCR || P.elastic == ELASTIC_FCR) {
+                svd3_robust(P.F, U, V, s3, e3, d3);
+                tau = tau_fcr(U, s3, e3, P.mu, P.lam);
+            } else if (!tau_nh(P.F, P.mu, P.lam, tau)) {
+                tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            }
             const float kf = 4.f * dt * P.vol * inv_dx * inv_dx;
             const float A[9] = {P.mass * P.C[0] - kf * tau.xx, P.mass * P.C[1] - kf * tau.xy,
                                 P.mass * P.C[2] - kf * tau.xz, P.mass * P.C[3] - kf * tau.xy,
@@ -862,30 +919,48 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout,
             for (int t = 0; t < 3; ++t) xa[t] = va[t] = 0.f;
 #pragma unroll
             for (int t = 0; t < 9; ++t) Ab[t] = 0.f;
-            for (int i = 0; i < 3; ++i)
+            // The P2G node contribution is w_i (m v + A (x_i - x_p)) and w_i m: its
+            // reverse gives the position adjoint sum_i wbar_i grad w_i -
+            // A^T sum_i w_i Pbar_i, with wbar_i = Pbar_i . (m v + A (x_i - x_p)) +
+            // m mbar_i.  The second term is A^T va / m (va = m sum_i w_i Pbar_i),
+            // taken once after the node loop.  The outer loop stays rolled; its
+            // weights are selected, not indexed, so that they stay in registers.
+            const float Pm[3] = {P.mass * P.v[0], P.mass * P.v[1], P.mass * P.v[2]};
+            float sPb[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int i = 0; i < 3; ++i) {
+                const float wi = i == 0 ? w[0][0] : (i == 1 ? w[0][1] : w[0][2]);
+                const float dwi = i == 0 ? dw[0][0] : (i == 1 ? dw[0][1] : dw[0][2]);
+                const float di = ((float)i - f[0]) * dx;
+                const float4 *gi = S.g + (b[0] + i) * GT * GT;
+#pragma unroll
                 for (int jj = 0; jj < 3; ++jj)
+#pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        const float wt = w[0][i] * w[1][jj] * w[2][k];
-                        const float gw[3] = {dw[0][i] * w[1][jj] * w[2][k] * inv_dx, w[0][i] * dw[1][jj] * w[2][k] * inv_dx,
-                                             w[0][i] * w[1][jj] * dw[2][k] * inv_dx};
-                        const float dp[3] = {((float)i - f[0]) * dx, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
-                        const float4 g = S.g[((b[0] + i) * GT + (b[1] + jj)) * GT + (b[2] + k)];
+                        const float wjk = w[1][jj] * w[2][k];
+                        const float wt = wi * wjk;
+                        const float gw[3] = {dwi * wjk, wi * dw[1][jj] * w[2][k], wi * w[1][jj] * dw[2][k]};
+                        const float dp[3] = {di, ((float)jj - f[1]) * dx, ((float)k - f[2]) * dx};
+                        const float4 g = gi[(b[1] + jj) * GT + (b[2] + k)];
                         const float Pb[3] = {g.x, g.y, g.z};
                         float wbar = g.w * P.mass;
 #pragma unroll
                         for (int r = 0; r < 3; ++r) {
                             const float Adr = A[3 * r] * dp[0] + A[3 * r + 1] * dp[1] + A[3 * r + 2] * dp[2];
-                            wbar += Pb[r] * (P.mass * P.v[r] + Adr);
-                            va[r] += wt * P.mass * Pb[r];
+                            wbar += Pb[r] * (Pm[r] + Adr);
+                            const float wp = wt * Pb[r];
+                            sPb[r] += wp;
 #pragma unroll
-                            for (int cc = 0; cc < 3; ++cc) Ab[3 * r + cc] += wt * Pb[r] * dp[cc];
+                            for (int cc = 0; cc < 3; ++cc) Ab[3 * r + cc] += wp * dp[cc];
                         }
 #pragma unroll
-                        for (int cc = 0; cc < 3; ++cc) {
-                            const float dpb = wt * (A[cc] * Pb[0] + A[3 + cc] * Pb[1] + A[6 + cc] * Pb[2]);
-                            xa[cc] += wbar * gw[cc] - dpb;
-                        }
+                        for (int cc = 0; cc < 3; ++cc) xa[cc] += wbar * inv_dx * gw[cc];
                     }
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) va[r] = P.mass * sPb[r];
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) xa[cc] -= A[cc] * sPb[0] + A[3 + cc] * sPb[1] + A[6 + cc] * sPb[2];
             // C enters A as m C; tau as -k tau (tau symmetric: use the symmetric part)
             float T[9];
 #pragma unroll
@@ -894,8 +969,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout,
                 for (int cc = 0; cc < 3; ++cc) T[3 * r + cc] = -0.5f * kf * (Ab[3 * r + cc] + Ab[3 * cc + r]);
 #pragma unroll
             for (int t = 0; t < 9; ++t) Fb[t] = 0.f;
-            if (P.elastic == ELASTIC_FCR) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
-            else if (P.elastic == ELASTIC_NH) nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
+            if (EL == ADJ_FCR || P.elastic == ELASTIC_FCR) fcr_adjoint(U, V, s3, e3, P.mu, P.lam, T, Fb, mubar, lambar);
+            else if (EL != ADJ_ALL || P.elastic == ELASTIC_NH) nh_adjoint(P.F, P.mu, P.lam, T, Fb, mubar, lambar);
             else more_adjoint(P.elastic, P.F, U, V, s3, e3, P.mu, P.lam, T, Fb, &mubar, &lambar);
         }
         // level 2 of chunk c + G has landed; the staged buffers are free
@@ -1080,15 +1155,38 @@ __global__ void k_tape_save(Dev D, int par, TapeSlot T, unsigned gcap, unsigned 
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
-// resident CTAs per SM of the reverse G2P and P2G kernels (the smaller)
-int adjoint_occupancy() {
-    int a = 0, b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_adj_g2p, ADJ_THREADS, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_adj_p2g, ADJ_THREADS, 0) != cudaSuccess) {
+// resident CTAs per SM of the reverse G2P (plasticity pl) and P2G
+// (elasticity el) kernels: the smaller of the two
+template <typename K> static int occupancy_of(K kernel) {
+    int a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, kernel, ADJ_THREADS, 0) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }
+    return a;
+}
+int adjoint_occupancy(int pl, int el) {
+    const int a = pl == ADJ_ELASTIC ? occupancy_of(k_adj_g2p<ADJ_ELASTIC>)
+                                    : (pl == ADJ_PLASTIC ? occupancy_of(k_adj_g2p<ADJ_PLASTIC>) : occupancy_of(k_adj_g2p<ADJ_ALL>));
+    const int b = el == ADJ_FCR ? occupancy_of(k_adj_p2g<ADJ_FCR>)
+                                : (el == ADJ_FCR_NH ? occupancy_of(k_adj_p2g<ADJ_FCR_NH>) : occupancy_of(k_adj_p2g<ADJ_ALL>));
     return std::max(1, std::min(a, b));
+}
+
+// the reverse G2P / P2G pair of the context's model set
+static void launch_adj_g2p(const mpm_ctx *ctx, const Dev &D, const float4 *ain, float4 *aout, cudaStream_t st) {
+    const AdjointStore &A = ctx->adj;
+    const int grid = ctx->grid_adj;
+    if (ctx->adj_pl == ADJ_ELASTIC) k_adj_g2p<ADJ_ELASTIC><<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
+    else if (ctx->adj_pl == ADJ_PLASTIC) k_adj_g2p<ADJ_PLASTIC><<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
+    else k_adj_g2p<ADJ_ALL><<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
+}
+static void launch_adj_p2g(const mpm_ctx *ctx, const Dev &D, float4 *aout, cudaStream_t st) {
+    const AdjointStore &A = ctx->adj;
+    const int grid = ctx->grid_adj;
+    if (ctx->adj_el == ADJ_FCR) k_adj_p2g<ADJ_FCR><<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
+    else if (ctx->adj_el == ADJ_FCR_NH) k_adj_p2g<ADJ_FCR_NH><<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
+    else k_adj_p2g<ADJ_ALL><<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
 }
 
 void free_adjoint(AdjointStore &a) {
@@ -1189,10 +1287,9 @@ static void adjoint_substep(mpm_ctx *ctx, float4 *state, float4 *ain, float4 *ao
     L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);                       // P2G of the recorded state
     L_prepare(ctx, 0, -1, 0, st, 1);                   // v = mask(mv/m + dt g), keeping (mv, m)
-    const int grid = ctx->grid_adj;
-    k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(D, ain, aout, A.gpar, A.gbar);
+    launch_adj_g2p(ctx, D, ain, aout, st);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);
-    k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(D, aout, A.gpar, A.gbar);
+    launch_adj_p2g(ctx, D, aout, st);
     k_adj_clear<<<ctx->grid_small, 256, 0, st>>>(D, A.gbar);
     ctx->launches += 4;
     D.rec = saved;
@@ -1346,10 +1443,9 @@ static Dev slot_dev(mpm_ctx *ctx, const TapeSlot &T) {
 static void adjoint_taped(mpm_ctx *ctx, const TapeSlot &T, float4 *ain, float4 *aout, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
     const Dev Dj = slot_dev(ctx, T);
-    const int grid = ctx->grid_adj;
-    k_adj_g2p<<<grid, ADJ_THREADS, 0, st>>>(Dj, ain, aout, A.gpar, A.gbar);
+    launch_adj_g2p(ctx, Dj, ain, aout, st);
     k_adj_grid<<<ctx->grid_small, 256, 0, st>>>(Dj, A.gbar);
-    k_adj_p2g<<<grid, ADJ_THREADS, 0, st>>>(Dj, aout, A.gpar, A.gbar);
+    launch_adj_p2g(ctx, Dj, aout, st);
     ctx->launches += 3;
 }
 

@@ -450,7 +450,15 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
         ctx->grid_sub[m] = ctx->sm_count * (occ > 0 ? occ : 1);
     }
     ctx->grid_small = ctx->sm_count * 8;
-    ctx->grid_adj = ctx->sm_count * adjoint_occupancy();
+    ctx->adj_pl = ADJ_ELASTIC;
+    ctx->adj_el = ADJ_FCR;
+    for (int m = 0; m < n_materials; ++m) {
+        if (pl[m] > 2) ctx->adj_pl = ADJ_ALL;
+        else if (pl[m] != 0) ctx->adj_pl = std::max(ctx->adj_pl, (int)ADJ_PLASTIC);
+        if (el[m] > 1) ctx->adj_el = ADJ_ALL;
+        else if (el[m] == 1) ctx->adj_el = std::max(ctx->adj_el, (int)ADJ_FCR_NH);
+    }
+    ctx->grid_adj = ctx->sm_count * adjoint_occupancy(ctx->adj_pl, ctx->adj_el);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         g_create_msg = std::string("create: ") + cudaGetErrorString(e);

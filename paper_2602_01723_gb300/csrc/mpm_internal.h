@@ -41,7 +41,11 @@ void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStr
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
 int substep_occupancy(int mode, int scatter, int chunk, bool xm);
 int substep_chunk_max();
-int adjoint_occupancy();
+// model sets of the reverse kernels: plasticity ADJ_ELASTIC (none) or
+// ADJ_PLASTIC (von Mises / Drucker-Prager); elasticity ADJ_FCR
+// (fixed-corotated) or ADJ_FCR_NH (and Neo-Hookean); ADJ_ALL: any model
+enum { ADJ_ELASTIC = 0, ADJ_PLASTIC = 1, ADJ_FCR = 0, ADJ_FCR_NH = 1, ADJ_ALL = 2 };
+int adjoint_occupancy(int pl, int el);
 
 // recorded trajectory and reverse-pass buffers
 struct AdjointStore {
@@ -121,6 +125,8 @@ struct mpm_ctx {
     int grid_sub[3] = {0, 0, 0};
     int grid_small = 0;
     int grid_adj = 0;             // reverse G2P / P2G kernels: SMs x resident CTAs per SM
+    int adj_pl = 2;               // plasticity of the reverse G2P kernel (ADJ_*)
+    int adj_el = 2;               // elasticity of the reverse P2G kernel (ADJ_*)
     long long recorded = 0;       // substeps recorded since the last load / reset
     bool record_broken = false;
     mpm::AdjointStore adj;
