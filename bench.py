@@ -164,6 +164,39 @@ def oracle_rate(sc, n_sub):
     return sc.n * n_sub / t, t, out
 
 
+def _oracle_instance_rate(job):
+    """One batch instance alone on the oracle (a worker of the all-core
+    baseline; runs in a spawned process)."""
+    idx, n_sub = job
+    from paper_2602_01723_gb300 import scenes
+    import oracle as orc
+    sc = scenes.batch_64()
+    sel = sc.instance == idx
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol[sel], sc.mat_id[sel] * 0, [sc.materials[idx]])
+    orc.run(cfg, orc.new_state(sc.x[sel], sc.v[sel]), mat, n_sub)
+    return int(sel.sum()) * n_sub
+
+
+def oracle_all_cores(n_inst=32, n_sub=10):
+    """The oracle as it stands on all host cores: independent instances of
+    the 64-instance batch (each its own problem on its own grid), one process
+    per core (spawned), over a bounded sample."""
+    import multiprocessing as mp
+    import oracle as orc
+    orc.build()
+    cores = min(os.cpu_count() or 1, n_inst)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_instance_rate, [(0, 1)] * cores)          # workers up, libraries loaded
+        t0 = time.perf_counter()
+        units = sum(pool.map(_oracle_instance_rate, [(i, n_sub) for i in range(n_inst)]))
+        t = time.perf_counter() - t0
+    return {"value": units / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d substeps of each of the first %d instances of the 64-instance batch, one process per "
+                      "core, FP64, %.1f s" % (n_sub, n_inst, t)}
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle timed on the host cores."""
     if "RANK" in os.environ and int(os.environ["RANK"]) != 0:
@@ -339,6 +372,15 @@ def run_ours(args):
     mc = guarded(mcis_leg, args, dev, flush)
     cf = guarded(configs_leg, args, dev, flush)
     rd = guarded(render_leg, args, sim, sc, dev, flush)
+    if rank == 0:
+        # every leg's result against the FP64 oracle, outside the timed regions
+        errs = guarded(fp64_errors, dev)
+        for leg, key in ((fb, "fwd_bwd"), (bg, "bgdo"), (mc, "mcis"), (rd, "render")):
+            leg["err_vs_fp64"] = errs.get(key, errs)
+        for name in ("cube_8k", "batch_64", "large_2m"):
+            if name in cf:
+                cf[name]["err_vs_fp64"] = errs.get(name, errs)
+        cpu_all = guarded(oracle_all_cores)
 
     if rank == 0:
         cpu_v, cpu_t = cpu[0], cpu[1]
@@ -360,6 +402,7 @@ def run_ours(args):
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d substeps of the %d-particle scene, FP64 oracle, 1 thread, %.1f s"
                                        % (ORACLE_SAMPLE_SUBSTEPS, n, cpu_t)},
+            "cpu_baseline_all_cores": cpu_all,
             "clocks": clk.summary(),
             "e2e": {"value": e2e_v, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
@@ -653,6 +696,146 @@ def render_leg(args, sim, sc, dev, flush):
     return {"gaussians": sc.n, "width": W, "height": H, "ms": t, "gaussians_per_s": sc.n / (t * 1e-3),
             "coverage": float((T < 0.5).float().mean().item()),
             "note": "CUDA events, median; includes the scratch allocation and the host read of the key count"}
+
+
+def fp64_errors(dev):
+    """The error of each leg's result against the FP64 oracle.  Both sides
+    start from the same seeded inputs; nothing the GPU computes is given to
+    the oracle.  Norms: positions max |dx| / dx; gradients
+    ||g - g_ref||_2 / ||g_ref||_2 per parameter kind; grids max |diff| over
+    max(|ref|, |m_ref| |g| dt); BGDO, MCIS and splat per-element maxima."""
+    import numpy as np
+    import torch
+    import oracle as orc
+    from paper_2602_01723_gb300 import scenes
+    from paper_2602_01723_gb300.sim import Simulator, mcis, render
+    orc.build()
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    out = {}
+
+    def setup(sc, params=None):
+        return (orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity),
+                orc.Material.from_table(sc.vol, sc.mat_id, sc.materials, params))
+
+    # cube_8k: the configured 100-substep run
+    sc = scenes.cube_8k()
+    s = Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(sc.n_substeps)
+    xg = s.positions().double().cpu().numpy()
+    s.close()
+    cfg, mat = setup(sc)
+    ref = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, sc.n_substeps)
+    out["cube_8k"] = {"x_max_dx": float(np.abs(xg - ref["x"]).max() / sc.dx), "substeps": sc.n_substeps}
+
+    # batch_64: the whole batch on the GPU for its 200 substeps; its smallest
+    # instance alone on the oracle
+    sc = scenes.batch_64()
+    s = Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(sc.n_substeps)
+    xg = s.positions().double().cpu().numpy()
+    s.close()
+    b = int(np.argmin(np.bincount(sc.instance, minlength=sc.n_instances)))
+    sel = sc.instance == b
+    cfg = orc.Cfg(sc.grid_res, sc.dx, sc.dt, sc.gravity)
+    mat = orc.Material.from_table(sc.vol[sel], sc.mat_id[sel] * 0, [sc.materials[b]])
+    ref = orc.run(cfg, orc.new_state(sc.x[sel], sc.v[sel]), mat, sc.n_substeps)
+    out["batch_64"] = {"x_max_dx": float(np.abs(xg[sel] - ref["x"]).max() / sc.dx), "instance": b,
+                       "particles": int(sel.sum()), "substeps": sc.n_substeps}
+
+    # large_2m: the P2G grid of a stressed seeded key frame, all 2M particles
+    # on the 256^3 grid, every node
+    sc = scenes.large_2m()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=47, vs=0.5, cs=2.0, fs=0.05)[0]
+    s = Simulator.from_scene(sc)
+    s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+    m, mv = s.debug_p2g()
+    m, mv = m[0].double().cpu().numpy(), mv[0].double().cpu().numpy()
+    s.close()
+    cfg, mat = setup(sc)
+    gm, gmv = orc.p2g(cfg, orc.new_state(sc.x, v, C, F), mat)
+    floor = np.abs(gm).max() * 9.8 * sc.dt
+    out["large_2m"] = {"grid_m_rel": float(np.abs(m - gm).max() / max(np.abs(gm).max(), floor)),
+                       "grid_mv_rel": float(np.abs(mv - gmv).max() / max(np.abs(gmv).max(), floor))}
+    del m, mv, gm, gmv
+
+    # fwd_bwd: the differentiable ball's 512-particle copy as configured (400
+    # substeps, checkpoint 20, ten frames), the same seeded cotangents on both
+    # sides
+    sc = scenes.ball_512()
+    frames = [int(f) for f in sc.frame_sub]
+    cot = np.random.default_rng(400).standard_normal((len(frames), sc.n, 3))
+    s = Simulator.from_scene(sc)
+    s.load_scene(sc)
+    s.step(sc.n_substeps, record=True)
+    xg = s.positions().double().cpu().numpy()
+    g = s.backward(frames, torch.as_tensor(cot, dtype=torch.float32)).double().cpu().numpy()
+    s.close()
+    cfg, mat = setup(sc, sc.params)
+    _, tape = orc.run(cfg, orc.new_state(sc.x, sc.v), mat, sc.n_substeps, tape=True)
+    _, gr = orc.backward(cfg, mat, tape, frames, cot)
+    out["fwd_bwd"] = {"workload": "ball_512 (the 512-particle, 16^3 copy)",
+                      "grad_logE_rel": rel(g[:, 0], gr[:, 0]), "grad_nu_rel": rel(g[:, 1], gr[:, 1]),
+                      "x_max_dx": float(np.abs(xg - tape[-1][:, 0:3]).max() / sc.dx),
+                      "cotangents": "seeded N(0, 1), the same on both sides"}
+
+    # bgdo: stage 2 from three seeded key frames of the 300k scene, every particle
+    sc = scenes.three_objects_300k()
+    keys = scenes.key_frames(sc, 3, k_seed=42, cs=2.0, fs=0.03)
+    s = Simulator.from_scene(sc)
+    for k, (v, C, F) in enumerate(keys):
+        s.load(sc.x, sc.vol, sc.mat_id, v=v, C=C, F=F)
+        s.snapshot(k)
+    got = {k: t.double().cpu().numpy() for k, t in s.bgdo([0, 1, 2], signals=True).items()}
+    s.close()
+    cfg, mat = setup(sc)
+    ref = orc.bgdo(cfg, [orc.new_state(sc.x, v, C, F) for v, C, F in keys], mat, label=sc.mat_id)
+    out["bgdo"] = {"G_max_abs": float(np.abs(got["G"] - ref["G"]).max()),
+                   "g_tau_max_rel": float((np.abs(got["g_tau"] - ref["g_tau"]) / np.maximum(np.abs(ref["g_tau"]), 1e-30)).max()),
+                   "delta_max_abs": float(np.abs(got["delta"] - ref["delta"]).max()),
+                   "sample": "every particle, three seeded key frames"}
+
+    # mcis: 1,500 sampled candidates against the oracle's brute force over
+    # their object's surface; every draw against the inverse CDF of the GPU's
+    # weights (exact integers)
+    c = scenes.mcis_case()
+    r = mcis(c["surf_off"], c["surf"], c["cand_off"], c["cand"], c["draw_off"], c["u"])
+    gd, gw, gp = (r[k].cpu().numpy() for k in ("d", "w", "picked"))
+    so, co, do = c["surf_off"], c["cand_off"], c["draw_off"]
+    rng = np.random.default_rng(9)
+    cut = 0.02 * np.sqrt(2 * np.log(1e6))
+    ed = ew = 0.0
+    draws_ok = True
+    for k in range(3):
+        idx = co[k] + rng.choice(co[k + 1] - co[k], 500, replace=False)
+        sub = orc.mcis([0, so[k + 1] - so[k]], c["surf"][so[k]:so[k + 1]], [0, 500], c["cand"][idx], [0, 0], [])
+        near = sub["d"] < cut
+        ed = max(ed, float((np.abs(gd[idx][near] - sub["d"][near]) / sub["d"][near].clip(1e-300)).max()))
+        ew = max(ew, float((np.abs(gw[idx] - sub["w"]) / sub["w"]).max()))
+        wq = np.floor(gw[co[k]:co[k + 1]] * 2.0 ** 40 + 0.5).astype(np.int64)
+        cum = np.cumsum(wq)
+        t = np.floor(c["u"][do[k]:do[k + 1]] * float(cum[-1])).astype(np.int64)
+        expect = co[k] + np.minimum(np.searchsorted(cum, t, side="right"), len(cum) - 1)
+        draws_ok = draws_ok and bool(np.array_equal(gp[do[k]:do[k + 1]], expect))
+    out["mcis"] = {"d_max_rel": ed, "w_max_rel": ew, "draws_exact": draws_ok,
+                   "sample": "1,500 candidates (500 per object); all 192k draws"}
+
+    # render: a tile-aligned 64 x 64 crop of the 1024 x 768 splat of the same
+    # deformed Gaussians; per pixel the excess over the order-ambiguity bound
+    sc = scenes.three_objects_300k()
+    v, C, F = scenes.key_frames(sc, 1, k_seed=81, fs=0.05)[0]
+    cov = orc.covariance(F, scenes.gaussian_covariances(sc)).astype(np.float32)
+    col, op = scenes.gaussian_appearance(sc)
+    W, H = 1024, 768
+    view, fx, fy, cx, cy = scenes.camera(W, H)
+    img, _ = render(sc.x, cov, col, op, view, fx, fy, cx, cy, W, H)
+    x0, y0 = 464, 400
+    ref, _, amb = orc.render(sc.x, cov, col, op, view, fx, fy, cx - x0, cy - y0, 64, 64, tie_eps=2.0 ** -21)
+    e = np.abs(img.cpu().numpy()[y0:y0 + 64, x0:x0 + 64] - ref).max(axis=2)
+    out["render"] = {"pixel_max_abs": float(e.max()), "pixel_max_abs_beyond_order_bound": float((e - amb).max()),
+                     "pixels_beyond_2e-4_and_bound": int(((e - amb) > 2e-4).sum()), "crop": "64 x 64 at (464, 400)"}
+    return out
 
 
 def fwd_bwd(args, dev, flush, world, dist):
