@@ -93,7 +93,6 @@ typedef struct {
     int32_t ckpt_every;         /* checkpoint interval k of the recorded forward pass (default 20) */
     int32_t chunk;              /* particles per work item of the substep kernel, <= 128 (0: 128);
                                    chunks of <= 64 run 64-thread CTAs, larger ones 128-thread CTAs */
-    int32_t threads;            /* unused (the substep kernel runs 128-thread CTAs) */
     int32_t scatter;            /* P2G scatter: 0 shared-memory float atomics, 1 int32 fixed-point
                                    shared-memory atomics (default), 2 direct global reductions */
     int32_t tape_grid;          /* reverse pass: 0 (default) keeps, for every state of a checkpoint
@@ -107,7 +106,7 @@ typedef struct {
                                    outgrows it).  1 keeps one bank of records only and rebuilds
                                    binning and grid in every reverse substep.  0 falls back to 1
                                    when its memory cannot be allocated. */
-    int32_t reserved[6];
+    int32_t reserved[7];        /* zero */
 } mpm_options;
 
 MPM_API mpm_status mpm_default_options(mpm_options *opt);
@@ -206,8 +205,9 @@ MPM_API mpm_status mpm_reduce_by_material(mpm_ctx *ctx, const float *per_particl
 MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, int32_t use_graph);
 
 /* Autotuner: times n_substeps >= 2 substeps from the current state for each
- * scatter strategy in {1, 2} and chunk size in {64, 128} (each trial
- * after a warm-up run), keeps the fastest, and restores the state.  out
+ * scatter strategy in {1, 2} and chunk size in {32, 64, 96, 128} (each
+ * trial after a warm-up run), keeps the fastest, and restores the state.  The
+ * grid tile (4x4x4-node blocks) is fixed by the data layout.  out
  * (nullable, host): chosen scatter, chosen chunk, best time in microseconds.
  * Synchronises the stream. */
 MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3], void *stream);

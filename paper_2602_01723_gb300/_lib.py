@@ -30,9 +30,9 @@ class mpm_material(ctypes.Structure):
 class mpm_options(ctypes.Structure):
     _fields_ = [("n_instances", ctypes.c_int32), ("bound", ctypes.c_int32), ("walls", ctypes.c_int32 * 6),
                 ("max_particles", ctypes.c_int64), ("max_active_blocks", ctypes.c_int64),
-                ("ckpt_every", ctypes.c_int32), ("chunk", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("ckpt_every", ctypes.c_int32), ("chunk", ctypes.c_int32),
                 ("scatter", ctypes.c_int32), ("tape_grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("reserved", ctypes.c_int32 * 7)]
 
 
 class mpm_bgdo_options(ctypes.Structure):

@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         results = list(ex.map(compile_one, SOURCES))
     objs = [o for o, _ in results]
     tmp = SO + ".tmp.%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))

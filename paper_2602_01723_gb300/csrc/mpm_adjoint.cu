@@ -1599,6 +1599,7 @@ using namespace mpm;
 
 extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const int32_t *frame_substep,
                                            const float *dL_dx, float *dL_dparams, float *dL_dstate0, void *stream) {
+    TraceRange trace_range("mpm_backward");
     if (!ctx) return MPM_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     if (!ctx->loaded || ctx->sticky) return ctx_fail(ctx, MPM_ERR_STATE, "no valid particle state");

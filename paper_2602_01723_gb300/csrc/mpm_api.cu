@@ -214,7 +214,7 @@ void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
             cudaEventRecord(ev[0], st);
         }
     }
-    launch_substep(ctx->D, mode, gpar, spar, ctx->grid_sub[mode], ctx->threads, st);
+    launch_substep(ctx->D, mode, gpar, spar, ctx->grid_sub[mode], st);
     ++ctx->launches;
     if (ev) cudaEventRecord(ev[1], st);
 }
@@ -398,7 +398,6 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     ctx->opt = o;
     ctx->table.assign(table, table + n_materials);
     ctx->total_blocks = total;
-    ctx->threads = 128;
     D.chunk = o.chunk > 0 ? std::min(o.chunk, substep_chunk_max()) : 128;
     mpm_status s = MPM_OK;
 #define CREATE_TRY(x)                              \
@@ -474,6 +473,7 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
 MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, const float *v, const float *C,
                                       const float *F, const float *vol, const int32_t *material_id,
                                       const int32_t *instance, const float *params, void *stream) {
+    TraceRange trace_range("mpm_load_particles");
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (n <= 0 || n > (1ll << 31) - 1 || !x || !vol || !material_id)
         return fail(ctx, MPM_ERR_INVALID_ARG, "n must be in [1, 2^31) and x, vol, material_id non-NULL");
@@ -518,6 +518,7 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
 }
 
 MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, void *stream) {
+    TraceRange trace_range("mpm_step");
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (n_substeps < 0) return fail(ctx, MPM_ERR_INVALID_ARG, "n_substeps < 0");
     if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state (load particles first)");
@@ -677,6 +678,7 @@ MPM_API mpm_status mpm_set_tuning(mpm_ctx *ctx, int32_t scatter, int32_t chunk, 
 }
 
 MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3], void *stream) {
+    TraceRange trace_range("mpm_autotune");
     if (!ctx || n_substeps < 2) return MPM_ERR_INVALID_ARG;
     if (!ctx->loaded || ctx->sticky) return fail(ctx, MPM_ERR_STATE, "no valid particle state");
     cudaStream_t st = S(stream);
@@ -697,10 +699,12 @@ MPM_API mpm_status mpm_autotune(mpm_ctx *ctx, int32_t n_substeps, int32_t out[3]
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bs = scat0, bc = chunk0;
-    const int scats[2] = {1, 2}, chunks[2] = {64, 128};
+    // scatter strategies x particles per work chunk (chunks of <= 64 run
+    // 64-thread CTAs at twice the CTAs per SM, larger ones 128-thread CTAs)
+    const int scats[2] = {1, 2}, chunks[4] = {32, 64, 96, 128};
     mpm_status s = MPM_OK;
     for (int a = 0; a < 2 && !s; ++a)
-        for (int b = 0; b < 2 && !s; ++b) {
+        for (int b = 0; b < 4 && !s; ++b) {
             if ((s = mpm_set_tuning(ctx, scats[a], chunks[b], graph0))) break;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && !s; ++rep) {   // first pass warms up (and captures the graph)
@@ -758,6 +762,7 @@ MPM_API mpm_status mpm_bgdo_default_options(mpm_bgdo_options *opt) {
 
 MPM_API mpm_status mpm_bgdo(mpm_ctx *ctx, int32_t n_keys, const int32_t *slots, const mpm_bgdo_options *opt,
                             float *G, float *log_E, float *g_tau, float *delta, void *stream) {
+    TraceRange trace_range("mpm_bgdo");
     if (!ctx) return MPM_ERR_INVALID_ARG;
     if (n_keys < 1 || n_keys > MPM_MAX_SNAPSHOTS || !slots)
         return fail(ctx, MPM_ERR_INVALID_ARG, "n_keys must be in [1, MPM_MAX_SNAPSHOTS] with a slot list");

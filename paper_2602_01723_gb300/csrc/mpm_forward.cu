@@ -984,8 +984,7 @@ template <int TPB> static void launch_tpb(const Dev &D, int mode, int gpar, int 
     else launch_sub<MODE_FUSED, 2, TPB, false>(D, gpar, spar, grid, st);
 }
 // the chunk size selects the CTA size: chunks of <= 64 particles run 64-thread CTAs
-void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st) {
-    (void)threads;
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st) {
     if (D.chunk <= 64) launch_tpb<64>(D, mode, gpar, spar, grid, st);
     else launch_tpb<128>(D, mode, gpar, spar, grid, st);
 }

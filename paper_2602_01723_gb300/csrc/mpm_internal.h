@@ -7,6 +7,8 @@
 #include <vector>
 
 #include "../../include/mpm.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "mpm_dev.cuh"
 #include "mpm_ptr.h"
 
@@ -25,6 +27,16 @@ struct LoadArgs {
     MatTable table;
 };
 
+// A named range on a profiler's timeline for the lifetime of the object: the
+// host-side phases of an entry point (load, forward substeps, reverse pass,
+// BGDO, autotuning).  Without an attached tool the calls return at once.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+
 inline int grid_for(long long n, int threads, int cap = 152 * 16) {
     long long g = (n + threads - 1) / threads;
     if (g < 1) g = 1;
@@ -36,7 +48,7 @@ void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st);
 void launch_bin(const Dev &D, cudaStream_t st);
 void launch_plan(const Dev &D, int bump_mask, cudaStream_t st);
 void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st);
-void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, int threads, cudaStream_t st);
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st);
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st);
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
 int substep_occupancy(int mode, int scatter, int chunk, bool xm);
@@ -121,7 +133,6 @@ struct mpm_ctx {
     bool loaded = false;
     mpm_status sticky = MPM_OK;
     std::string msg;
-    int threads = 256;
     int grid_sub[3] = {0, 0, 0};
     int grid_small = 0;
     int grid_adj = 0;             // reverse G2P / P2G kernels: SMs x resident CTAs per SM

@@ -34,7 +34,7 @@ class Simulator:
     """One simulation context (one or more independent grids)."""
 
     def __init__(self, grid_res, dx, dt, gravity, materials, n_instances=1, walls=None, bound=3, ckpt_every=20,
-                 chunk=0, threads=0, max_active_blocks=0, max_particles=0, scatter=1, tape_grid=0, device="cuda"):
+                 chunk=0, max_active_blocks=0, max_particles=0, scatter=1, tape_grid=0, device="cuda"):
         if np.isscalar(grid_res):
             grid_res = (grid_res,) * 3
         self.grid_res = tuple(int(r) for r in grid_res)
@@ -48,7 +48,6 @@ class Simulator:
                 opt.walls[i] = int(w)
         opt.ckpt_every = int(ckpt_every)
         opt.chunk = int(chunk)
-        opt.threads = int(threads)
         opt.scatter = int(scatter)
         opt.tape_grid = int(tape_grid)
         opt.max_active_blocks = int(max_active_blocks)

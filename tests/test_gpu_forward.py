@@ -320,3 +320,26 @@ def test_three_objects_full_size_30_substeps(orc, sim_mod):
     ex = np.abs(got["x"] - ref["x"]).max() / sc.dx
     print("three objects, 30 substeps: x %.3g dx" % ex)
     assert ex < 1e-5, ex
+
+
+def test_allocation_failure_reports_oom_and_leaves_a_destroyable_context(sim_mod):
+    """A particle capacity far beyond device memory (2^40 particles, 128 TB
+    of records): mpm_load_particles returns MPM_ERR_OOM from the failed device
+    allocation before any launch, the context reports it in mpm_last_error
+    and is destroyed cleanly, and a fresh context on the device then runs."""
+    from paper_2602_01723_gb300 import _lib as L
+    sc = scenes.cube_8k()
+    s = sim_mod.Simulator.from_scene(sc, max_particles=1 << 40)
+    with pytest.raises(L.MpmError) as e:
+        s.load_scene(sc)
+    assert e.value.status == 2, (e.value.status, str(e.value))            # MPM_ERR_OOM
+    assert b"cudaMalloc" in L.lib().mpm_last_error(s.ctx)
+    with pytest.raises(L.MpmError):
+        s.step(1)                                                            # nothing loaded
+    s.close()
+    s2 = sim_mod.Simulator.from_scene(sc)
+    s2.load_scene(sc)
+    s2.step(5)
+    s2.sync()
+    assert s2.stats()["device_error"] == 0
+    s2.close()

@@ -38,7 +38,7 @@ def test_autotuner_picks_a_valid_setting_and_restores_the_state(sim_mod):
     s.load_scene(sc)
     x0 = s.positions().clone()
     r = s.autotune(10)
-    assert r["scatter"] in (1, 2) and r["chunk"] in (64, 128) and r["best_us"] > 0
+    assert r["scatter"] in (1, 2) and r["chunk"] in (32, 64, 96, 128) and r["best_us"] > 0
     assert torch.equal(s.positions(), x0)
     s.step(20)
     s.sync()
