@@ -286,7 +286,7 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, 
                     cudaGetLastError();
                     return fail(ctx, MPM_ERR_CUDA, "graph launch failed");
                 }
-                ctx->launches += 8;
+                ctx->launches += 6;   // two substeps: prepare, fused substep and plan each
             }
         }
     }
