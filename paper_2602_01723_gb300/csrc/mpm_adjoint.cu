@@ -901,10 +901,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout,
             float U[9], V[9], s3[3], e3[3], d3[3];
             Sym tau;
             if (EL == ADJ_ALL) {
-                if (elastic_needs_svd(P.elastic)) svd3_robust(P.F, U, V, s3, e3, d3);
+                if (elastic_needs_svd(P.elastic)) svd3_robust_cold(P.F, U, V, s3, e3, d3);
                 if (!kirchhoff(P.elastic, P.F, U, s3, e3, P.mu, P.lam, tau)) tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
             } else if (EL == ADJ_FCR || P.elastic == ELASTIC_FCR) {
-                svd3_robust(P.F, U, V, s3, e3, d3);
+                svd3_robust_cold(P.F, U, V, s3, e3, d3);
                 tau = tau_fcr(U, s3, e3, P.mu, P.lam);
             } else if (!tau_nh(P.F, P.mu, P.lam, tau)) {
                 tau = Sym{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};

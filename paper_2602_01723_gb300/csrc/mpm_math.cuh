@@ -264,6 +264,44 @@ __device__ bool svd3(const T F[9], T U[9], T V[9], T s[3], T e[3], T d[3]) {
 
 // FP32 SVD with the FP64 branch for rank-deficient or non-finite input.
 // Returns 0 on the FP32 path, 1 when the FP64 branch ran, 2 when both failed.
+// The FP64 branch out of line, for kernels whose instruction footprint
+// matters more than a call on the rare slow path.  Arguments and results
+// pass by value, so that the caller's arrays stay in registers on the fast
+// path; status 1 FP64 ok, 2 FP64 failed.
+struct Svd3Out {
+    float U[9], V[9], s[3], e[3], d[3];
+    int status;
+};
+struct Mat3f {
+    float a[9];
+};
+static __device__ __noinline__ Svd3Out svd3_fp64_out(Mat3f F) {
+    double Fd[9], Ud[9], Vd[9], sd[3], ed[3], dd[3];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Fd[i] = (double)F.a[i];
+    const bool ok = svd3<double>(Fd, Ud, Vd, sd, ed, dd);
+    Svd3Out o;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { o.U[i] = (float)Ud[i]; o.V[i] = (float)Vd[i]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { o.s[i] = (float)sd[i]; o.e[i] = (float)ed[i]; o.d[i] = (float)dd[i]; }
+    o.status = ok ? 1 : 2;
+    return o;
+}
+__device__ __forceinline__ int svd3_robust_cold(const float F[9], float U[9], float V[9], float s[3], float e[3],
+                                                float d[3]) {
+    if (svd3<float>(F, U, V, s, e, d)) return 0;
+    Mat3f Fm;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Fm.a[i] = F[i];
+    const Svd3Out o = svd3_fp64_out(Fm);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) { U[i] = o.U[i]; V[i] = o.V[i]; }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) { s[i] = o.s[i]; e[i] = o.e[i]; d[i] = o.d[i]; }
+    return o.status;
+}
+
 __device__ __forceinline__ int svd3_robust(const float F[9], float U[9], float V[9], float s[3], float e[3],
                                            float d[3]) {
     if (svd3<float>(F, U, V, s, e, d)) return 0;
