@@ -178,7 +178,10 @@ MPM_API mpm_status mpm_sync(mpm_ctx *ctx, void *stream);
  * word, [7] grid pool capacity (blocks), [8] kernels launched by this
  * context so far, [9] grid-tape pool blocks per recorded state (0: no grid
  * tape), [10] reverse passes run again because a state's grid did not fit
- * its grid-tape slot; [11..15] zero. */
+ * its grid-tape slot, [11] particles the forward's direct binning placed in
+ * one-particle work items since the last load (their block's list was full
+ * or beyond the lists), [12] particles per block list and [13] block lists
+ * of that binning (sized at each load); [14..15] zero. */
 MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream);
 
 /* Tracing of the substep kernel.  When ms and count are not NULL, first

@@ -162,7 +162,8 @@ def mpm_stats(ctx, stream):
     c = (ctypes.c_int64 * 16)()
     check(lib().mpm_stats(ctx, c, stream), ctx)
     keys = ["particles", "occupied_blocks", "active_blocks", "chunks", "fp64_svd_fallbacks", "recorded",
-            "device_error", "pool_blocks", "launches", "tape_grid_blocks", "tape_grid_reruns"]
+            "device_error", "pool_blocks", "launches", "tape_grid_blocks", "tape_grid_reruns", "overflow_particles",
+            "list_capacity", "list_blocks"]
     return dict(zip(keys, list(c)))
 
 

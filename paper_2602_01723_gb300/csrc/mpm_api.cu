@@ -162,6 +162,51 @@ mpm_status ensure_particles(mpm_ctx *ctx, long long n) {
 
 cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 
+// Lists of the direct binning, sized from the binning of the load that just
+// completed: per block max(64, 1.5 x the largest block count) particles (a
+// multiple of 32), for up to 8 x the occupied blocks + 256 pool slots (the
+// active blocks around the occupied ones number about 3 x); overflow entries
+// and work items for every particle.  A later compression beyond these sizes
+// costs one-particle work items (counted in mpm_stats), not correctness.
+mpm_status ensure_direct(mpm_ctx *ctx, cudaStream_t st) {
+    Dev &D = ctx->D;
+    unsigned c[CTR_COUNT];
+    CK(cudaMemcpyAsync(c, D.ctr, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const unsigned maxcnt = c[CTR_MAX_COUNT], nocc = c[CTR_N_OCC];
+    unsigned cap = std::max(64u, (maxcnt + maxcnt / 2 + 31u) / 32u * 32u);
+    cap = std::min(cap, 8192u);
+    const unsigned long long blocks = std::min<unsigned long long>(ctx->pool_blocks, 8ull * nocc + 256ull);
+    const size_t slist = (size_t)blocks * cap;
+    const size_t n = (size_t)ctx->cap;
+    const size_t chunks = n / 16 + (size_t)std::min<long long>(ctx->cap, ctx->total_blocks) + 1 + n;
+    mpm_status s;
+    bool grew = false;
+    for (int k = 0; k < 2; ++k) {
+        if (slist > ctx->slist_alloc && (s = dalloc(ctx, &D.slist[k], slist, false))) return s;
+        if (2 * n > ctx->ovf_alloc && (s = dalloc(ctx, &D.ovf[k], 2 * n, false))) return s;
+        if ((size_t)ctx->total_blocks > ctx->occd_alloc && (s = dalloc(ctx, &D.occd[k], (size_t)ctx->total_blocks, false)))
+            return s;
+        if (chunks > ctx->chunksd_alloc && (s = dalloc(ctx, &D.chunksd[k], chunks, false))) return s;
+    }
+    if (slist > ctx->slist_alloc) { ctx->slist_alloc = slist; grew = true; }
+    if (2 * n > ctx->ovf_alloc) { ctx->ovf_alloc = 2 * n; grew = true; }
+    if ((size_t)ctx->total_blocks > ctx->occd_alloc) { ctx->occd_alloc = (size_t)ctx->total_blocks; grew = true; }
+    if (chunks > ctx->chunksd_alloc) { ctx->chunksd_alloc = chunks; grew = true; }
+    if (D.slist_cap != cap || D.slist_blocks != (unsigned)(ctx->slist_alloc / cap)) grew = true;
+    // every list entry a work item can reach is written by the binning that
+    // made the item; cleared here all the same, so that any entry is a
+    // particle index of this load
+    for (int k = 0; k < 2; ++k) CK(cudaMemsetAsync(D.slist[k], 0, ctx->slist_alloc * sizeof(unsigned), st));
+    D.slist_cap = cap;
+    D.slist_blocks = (unsigned)std::min<size_t>(ctx->slist_alloc / cap, ctx->pool_blocks);
+    D.ovf_cap = (unsigned)(ctx->ovf_alloc / 2);
+    D.max_chunks_d = (unsigned)std::min<size_t>(ctx->chunksd_alloc, 0xffffffffu);
+    if (grew) ++ctx->generation;   // kernel arguments changed: recapture the graphs
+    ctx->direct_ready = true;
+    return MPM_OK;
+}
+
 }  // namespace
 
 // chunk list large enough for the current chunk size and particle capacity
@@ -198,7 +243,12 @@ void L_bin(mpm_ctx *ctx, cudaStream_t st) {
     ++ctx->launches;
     ctx->bins_pending = true;
 }
-void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
+void L_between(mpm_ctx *ctx, int upd, int act, cudaStream_t st) {
+    launch_between(ctx->D, upd, act, ctx->grid_small, st);
+    ++ctx->launches;
+    ctx->bins_pending = false;
+}
+void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st, bool direct, int in_par) {
     cudaEvent_t *ev = nullptr;
     if (ctx->trace_on) {
         std::vector<cudaEvent_t> &pool = ctx->trace_ev[mode];
@@ -214,7 +264,14 @@ void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st) {
             cudaEventRecord(ev[0], st);
         }
     }
-    launch_substep(ctx->D, mode, gpar, spar, ctx->grid_sub[mode], st);
+    Dev Dc = ctx->D;
+    if (in_par >= 0) {   // the work items and lists of the direct binning into buffer in_par
+        Dc.chunks = ctx->D.chunksd[in_par];
+        Dc.chunk_ctr = CTR_D_CH + in_par;
+        Dc.sorted = ctx->D.slist[in_par];
+        Dc.ovf_in = ctx->D.ovf[in_par];
+    }
+    launch_substep(Dc, mode, gpar, spar, ctx->grid_sub[mode], direct, st);
     ++ctx->launches;
     if (ev) cudaEventRecord(ev[1], st);
 }
@@ -228,12 +285,21 @@ static void middle_substep(mpm_ctx *ctx, int par, cudaStream_t st) {
     L_plan(ctx, 1 << par, st);
 }
 
-// CUDA graph of two steady-state substeps (parity 0 then 1).  It is captured
+// one steady-state substep with direct binning: between-substep work for
+// buffer par (grid update, work items of the last binning, activation of the
+// other buffer), then the fused G2P + P2G binning into the other buffer
+static void middle_direct(mpm_ctx *ctx, int par, cudaStream_t st) {
+    L_between(ctx, par, par ^ 1, st);
+    L_substep(ctx, 1, par, par ^ 1, st, true, par);
+}
+
+// CUDA graph of two steady-state substeps (parity 0 then 1; with direct
+// binning, which starts at substep 1, parity 1 then 0).  It is captured
 // on a library-owned stream (the legacy default stream cannot be captured)
 // the first time it is needed for this particle count and these buffers, and
 // replayed on the caller's stream.
-static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st) {
-    const long long key = (long long)ctx->D.n * 1000003ll + ctx->generation;
+static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st, bool direct) {
+    const long long key = ((long long)ctx->D.n * 1000003ll + ctx->generation) * 2 + (direct ? 1 : 0);
     if (ctx->graph2 && ctx->graph_key == key) return ctx->graph2;
     if (ctx->graph2) { cudaGraphExecDestroy(ctx->graph2); ctx->graph2 = nullptr; }
     cudaStreamCaptureStatus cs;
@@ -250,8 +316,13 @@ static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st) {
     cudaGraph_t g = nullptr;
     cudaStream_t cst = ctx->cap_stream;
     if (cudaStreamBeginCapture(cst, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaGetLastError(); return nullptr; }
-    middle_substep(ctx, 0, cst);
-    middle_substep(ctx, 1, cst);
+    if (direct) {
+        middle_direct(ctx, 1, cst);
+        middle_direct(ctx, 0, cst);
+    } else {
+        middle_substep(ctx, 0, cst);
+        middle_substep(ctx, 1, cst);
+    }
     if (cudaStreamEndCapture(cst, &g) != cudaSuccess || !g) { cudaGetLastError(); ctx->launches = l0; return nullptr; }
     cudaGraphExec_t ex = nullptr;
     if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) { cudaGetLastError(); ex = nullptr; }
@@ -275,11 +346,40 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, 
     L_plan(ctx, 3, st);               // epochs for buffer 0 (P2G below) and 1 (first fused substep)
     L_prepare(ctx, -1, 0, 1, st);
     L_substep(ctx, 0, 0, 0, st);
-    int s = 0;
     const int middle = n_sub - 1;
+    // Direct binning (forward runs without a tape, scatter strategies 1 and
+    // 2): the fused substeps place each particle straight into its new
+    // block's list, and one k_between launch (no scan, no sort) prepares the
+    // next substep.  Substep 0 runs on the plan above.
+    if (!tape && ctx->direct_ready && ctx->D.scatter != 0 && middle > 0) {
+        CK(cudaMemsetAsync(ctx->D.ctr + CTR_D_OCC, 0, 6 * sizeof(unsigned), st));
+        L_prepare(ctx, 0, 1, 0, st);
+        L_substep(ctx, 1, 0, 1, st, true, -1);
+        int s = 1;
+        if (ctx->use_graph && !ctx->trace_on && middle >= 5 && !stream_capturing(st)) {
+            cudaGraphExec_t ex = graph_pair(ctx, st, true);
+            if (ex) {
+                for (; s + 1 < middle; s += 2) {
+                    if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+                        cudaGetLastError();
+                        return fail(ctx, MPM_ERR_CUDA, "graph launch failed");
+                    }
+                    ctx->launches += 4;   // two substeps: between + fused substep each
+                }
+            }
+        }
+        for (; s < middle; ++s) middle_direct(ctx, s & 1, st);
+        L_between(ctx, middle & 1, -1, st);              // work items of the last binning
+        L_substep(ctx, 2, middle & 1, 0, st, false, middle & 1);
+        ctx->bins_pending = true;     // the last substep binned the new positions (for a sort)
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(ctx, MPM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
+        return MPM_OK;
+    }
+    int s = 0;
     // inside the caller's stream capture the substeps go straight into its graph
     if (ctx->use_graph && !ctx->trace_on && !tape && middle >= 4 && !stream_capturing(st)) {
-        cudaGraphExec_t ex = graph_pair(ctx, st);
+        cudaGraphExec_t ex = graph_pair(ctx, st, false);
         if (ex) {
             for (; s + 1 < middle; s += 2) {
                 if (cudaGraphLaunch(ex, st) != cudaSuccess) {
@@ -378,6 +478,7 @@ MPM_API mpm_status mpm_create(const int32_t grid_res[3], float dx, float dt, con
     cudaGetDevice(&ctx->device);
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     std::memset(&ctx->D, 0, sizeof(Dev));
+    ctx->D.chunk_ctr = CTR_N_CHUNKS;
     Dev &D = ctx->D;
     for (int d = 0; d < 3; ++d) {
         ctx->R[d] = grid_res[d];
@@ -503,6 +604,7 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     CK(cudaMemsetAsync(D.err, 0, sizeof(unsigned), st));
     CK(cudaMemsetAsync(D.bcount, 0, (size_t)ctx->total_blocks * sizeof(unsigned), st));
     CK(cudaMemsetAsync(D.ctr + CTR_N_OCC, 0, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(D.ctr + CTR_D_OVF_TOTAL, 0, 2 * sizeof(unsigned), st));   // and CTR_MAX_COUNT
     launch_load(D, a, st);
     ++ctx->launches;
     L_bin(ctx, st);
@@ -513,8 +615,11 @@ MPM_API mpm_status mpm_load_particles(mpm_ctx *ctx, int64_t n, const float *x, c
     ctx->record_broken = false;
     if (cap) return MPM_OK;   // device errors surface at the next synchronising call
     s = check_device_error(ctx, st);
-    if (s) ctx->loaded = false;
-    return s;
+    if (s) {
+        ctx->loaded = false;
+        return s;
+    }
+    return ensure_direct(ctx, st);
 }
 
 MPM_API mpm_status mpm_step(mpm_ctx *ctx, int32_t n_substeps, int32_t record, void *stream) {
@@ -583,6 +688,9 @@ MPM_API mpm_status mpm_stats(mpm_ctx *ctx, int64_t counters[16], void *stream) {
     counters[8] = ctx->launches;
     counters[9] = ctx->adj.gt ? ctx->adj.gt_pool : 0;
     counters[10] = ctx->adj.gt_reruns;
+    counters[11] = c[CTR_D_OVF_TOTAL];
+    counters[12] = ctx->direct_ready ? ctx->D.slist_cap : 0;
+    counters[13] = ctx->direct_ready ? ctx->D.slist_blocks : 0;
     return MPM_OK;
 }
 
@@ -628,6 +736,7 @@ MPM_API mpm_status mpm_destroy(mpm_ctx *ctx) {
     dfree(D.occ); dfree(D.plan); dfree(D.chunks); dfree(D.ctr); dfree(D.err);
     for (int k = 0; k < 2; ++k) {
         dfree(D.page[k]); dfree(D.page_epoch[k]); dfree(D.active[k]); dfree(D.gmv[k]); dfree(D.gv[k]);
+        dfree(D.slist[k]); dfree(D.ovf[k]); dfree(D.occd[k]); dfree(D.chunksd[k]);
     }
     dfree(ctx->mE); dfree(ctx->mnu); dfree(ctx->mrho); dfree(ctx->myield); dfree(ctx->malpha);
     dfree(ctx->mel); dfree(ctx->mpl);

@@ -78,8 +78,21 @@ struct Dev {
     unsigned *bstart;      // total blocks: first sorted slot of each occupied block
     unsigned *occ;         // occupied blocks being collected by the binning kernel
     unsigned *plan;        // occupied blocks of the grouping in use
-    int4 *chunks;          // work items: (block key, first sorted slot, count, 0)
+    int4 *chunks;          // work items the substep kernel reads: (block key, first index, count, list)
     unsigned *ctr;         // device counters, see CTR_*
+    int chunk_ctr;         // index in ctr of the number of work items (CTR_N_CHUNKS unless direct)
+    // list 0 of a work item: `sorted` (the counting sort, or a direct binning's
+    // per-block lists); list 1: the overflow entries (particle, block key) of a
+    // direct binning, one particle per work item
+    const unsigned *ovf_in;
+    // direct binning (the steady-state substeps of a forward run): the fused
+    // kernel places each particle straight into the list of its new block,
+    // at the block's pool slot in the scatter buffer; per grid buffer:
+    unsigned *slist[2];    // slist_blocks lists of slist_cap particle indices
+    unsigned *ovf[2];      // (particle, block key) of particles whose list was full or beyond slist_blocks
+    unsigned *occd[2];     // occupied blocks of the binning
+    int4 *chunksd[2];      // work items of the binning
+    unsigned slist_cap, slist_blocks, ovf_cap, max_chunks_d;
     // grid buffers (index = parity)
     int *page[2];
     unsigned *page_epoch[2];
@@ -103,7 +116,12 @@ enum {
     CTR_EPOCH_OF = 4,      // [4], [5]: epoch of grid buffer 0 / 1
     CTR_N_ACTIVE = 6,      // [6], [7]: active blocks of grid buffer 0 / 1
     CTR_FALLBACKS = 8,     // FP64 SVD branch count
-    CTR_COUNT = 16
+    CTR_D_OCC = 16,        // [16], [17]: occupied blocks of the direct binning into buffer 0 / 1
+    CTR_D_OVF = 18,        // [18], [19]: its overflow entries
+    CTR_D_CH = 20,         // [20], [21]: its work items
+    CTR_D_OVF_TOTAL = 22,  // particles placed in overflow entries since the last load
+    CTR_MAX_COUNT = 23,    // largest block count of the last full binning (k_bin)
+    CTR_COUNT = 32
 };
 
 __device__ __forceinline__ unsigned block_key(const Dev &D, int inst, int bx, int by, int bz) {

@@ -123,6 +123,33 @@ __device__ __forceinline__ void bin_end(const Dev &D, const BinTicket &t, unsign
 __device__ __forceinline__ void bin_particle(const Dev &D, unsigned mask, unsigned p, unsigned key) {
     BinTicket t = bin_begin(D, mask, key);
     bin_end(D, t, p);
+    // the largest block count (sizes the per-block lists of the direct binning)
+    if ((int)(threadIdx.x & 31) == __ffs(t.peers) - 1) atomicMax(&D.ctr[CTR_MAX_COUNT], t.base + __popc(t.peers));
+}
+
+// Direct binning into the lists of grid buffer par: the particle of rank r in
+// a block with pool slot sl goes to slist[par][sl * slist_cap + r]; one whose
+// list is full (r >= slist_cap) or whose slot lies beyond the lists (or is not
+// active, a broken grouping already reported) goes to an overflow entry.
+__device__ __forceinline__ void bin_end_direct(const Dev &D, const BinTicket &t, unsigned p, int slot, int par) {
+    const int leader = __ffs(t.peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader && t.base == 0) {
+        const unsigned i = atomicAdd(&D.ctr[CTR_D_OCC + par], 1u);
+        D.occd[par][i] = t.key;
+    }
+    const unsigned rank = __shfl_sync(t.peers, t.base, leader) + __popc(t.peers & lanemask_lt());
+    if (slot >= 0 && (unsigned)slot < D.slist_blocks && rank < D.slist_cap) {
+        D.slist[par][(size_t)slot * D.slist_cap + rank] = p;
+    } else {
+        const unsigned o = atomicAdd(&D.ctr[CTR_D_OVF + par], 1u);
+        atomicAdd(&D.ctr[CTR_D_OVF_TOTAL], 1u);
+        if (o < D.ovf_cap) {
+            D.ovf[par][2 * (size_t)o] = p;
+            D.ovf[par][2 * (size_t)o + 1] = t.key;
+        } else {
+            set_err(D, ERRB_CAPACITY);
+        }
+    }
 }
 
 __global__ void k_bin(Dev D) {
@@ -294,6 +321,104 @@ __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep
 }
 
 // ---------------------------------------------------------------------------
+// between two substeps of direct binning (one launch, no scan and no sort):
+//   * the grid update of buffer upd, which the last substep's scatter filled
+//     (App. A: v = mv/m + dt g, walls), clearing its momentum;
+//   * the work items of the binning that substep made: each occupied block's
+//     list (at its pool slot in upd) in items of <= chunk particles, and one
+//     item per overflow entry;
+//   * the activation of buffer act (< 0: none) around the occupied blocks, for
+//     the next scatter, under a fresh epoch: EPOCH_OF[upd] + 1, above every
+//     epoch either buffer holds (upd's is the latest opened).
+// The counters it reads are not written in this launch; thread 0 of CTA 0
+// resets the ones the next substep's binning starts from.
+// ---------------------------------------------------------------------------
+__global__ void k_between(Dev D, int upd, int act) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const unsigned nocc = D.ctr[CTR_D_OCC + upd];
+    const unsigned novf = min(D.ctr[CTR_D_OVF + upd], D.ovf_cap);
+    const unsigned ep_upd = D.ctr[CTR_EPOCH_OF + upd];
+    const unsigned ep_new = ep_upd + 1u;
+    const unsigned CH = (unsigned)D.chunk;
+    if (tid == 0) {
+        D.ctr[CTR_N_PLAN] = nocc;
+        if (act >= 0) {
+            D.ctr[CTR_EPOCH] = ep_new;
+            D.ctr[CTR_EPOCH_OF + act] = ep_new;
+            D.ctr[CTR_D_OCC + act] = 0;
+            D.ctr[CTR_D_OVF + act] = 0;
+        }
+    }
+    // grid update of upd
+    {
+        const unsigned lim = min(D.ctr[CTR_N_ACTIVE + upd], D.max_active) * BLK_NODES;
+        for (unsigned i = tid; i < lim; i += stride) {
+            const unsigned slot = i >> 6, l = i & 63u;
+            int inst, bx, by, bz;
+            key_coords(D, D.active[upd][slot], inst, bx, by, bz);
+            const int I = bx * BLK + (int)(l >> 4), J = by * BLK + (int)((l >> 2) & 3u), K = bz * BLK + (int)(l & 3u);
+            const float4 a = D.gmv[upd][i];
+            float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.w > 0.f) {
+                const float im = 1.f / a.w;
+                float u0 = a.x * im + D.dt * D.g[0], u1 = a.y * im + D.dt * D.g[1], u2 = a.z * im + D.dt * D.g[2];
+                apply_walls(D, I, J, K, u0, u1, u2);
+                out = make_float4(u0, u1, u2, a.w);
+            }
+            D.gv[upd][i] = out;
+            D.gmv[upd][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    // work items: the lists of the occupied blocks
+    for (unsigned i = tid; i < nocc; i += stride) {
+        const unsigned key = D.occd[upd][i];
+        const unsigned cnt = D.bcount[key];
+        D.bcount[key] = 0;
+        const int sl = D.page_epoch[upd][key] == ep_upd ? D.page[upd][key] : -1;
+        const unsigned main = (sl >= 0 && (unsigned)sl < D.slist_blocks) ? min(cnt, D.slist_cap) : 0u;
+        const unsigned nch = (main + CH - 1) / CH;
+        if (nch == 0) continue;
+        const unsigned c0 = atomicAdd(&D.ctr[CTR_D_CH + upd], nch);
+        for (unsigned j = 0; j < nch; ++j) {
+            if (c0 + j < D.max_chunks_d)
+                D.chunksd[upd][c0 + j] = make_int4((int)key, (int)((unsigned)sl * D.slist_cap + j * CH),
+                                                   (int)min(CH, main - j * CH), 0);
+            else
+                set_err(D, ERRB_CAPACITY);
+        }
+    }
+    // one work item per overflow entry (list 1)
+    for (unsigned o = tid; o < novf; o += stride) {
+        const unsigned c = atomicAdd(&D.ctr[CTR_D_CH + upd], 1u);
+        if (c < D.max_chunks_d) D.chunksd[upd][c] = make_int4((int)D.ovf[upd][2 * o + 1], (int)(2 * o), 1, 1);
+        else set_err(D, ERRB_CAPACITY);
+    }
+    // activation of act around the occupied blocks
+    if (act >= 0) {
+        const unsigned items = nocc * 27u;
+        for (unsigned i = tid; i < items; i += stride) {
+            const unsigned b = i / 27u, o = i - b * 27u;
+            int inst, bx, by, bz;
+            key_coords(D, D.occd[upd][b], inst, bx, by, bz);
+            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
+            if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
+            const unsigned nk = block_key(D, inst, nx, ny, nz);
+            const unsigned old = atomicMax(&D.page_epoch[act][nk], ep_new);
+            if (old != ep_new) {
+                const unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + act], 1u);
+                if (slot < D.max_active) {
+                    D.page[act][nk] = (int)slot;
+                    D.active[act][slot] = nk;
+                } else {
+                    D.page[act][nk] = -1;
+                    set_err(D, ERRB_CAPACITY);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // the substep kernel
 //   MODE_P2G: scatter at the current positions (first substep of a call)
 //   MODE_FUSED: G2P(s) + update + return map + stress + P2G(s+1) + binning
@@ -392,7 +517,7 @@ template <int TPB, bool GATHER, bool SCATTER>
 __device__ __forceinline__ void stage_level2(const Dev &D, SubstepSmem<TPB> &S, int4 ch, int gpar, int spar,
                                              unsigned ep_g, unsigned ep_s) {
     const int tid = threadIdx.x;
-    if (tid < ch.z) cp_async4(&S.pidx[tid], D.sorted + ch.y + tid);
+    if (tid < ch.z) cp_async4(&S.pidx[tid], (ch.w ? D.ovf_in : D.sorted) + ch.y + tid);
     int inst, bx, by, bz;
     key_coords(D, (unsigned)ch.x, inst, bx, by, bz);
     const int t = tid - (TPB - 64 > 0 ? 64 : 0);    // the lookups go to the last warps of the CTA
@@ -449,17 +574,26 @@ __device__ __forceinline__ void stage_slots(SubstepSmem<TPB> &S, int buf, unsign
 // TPB: threads per CTA = largest chunk (one particle per thread); 64 or 128.
 // Both variants cap registers at 128 (16 warps per SM); the 64-thread one
 // runs twice as many independent CTAs, which overlap each other's staging.
+// DB (fused mode): the new binning goes straight into the scatter buffer's
+// per-block lists (bin_end_direct) instead of keys and ranks for a sort.
 // XM: the further constitutive models (StVK, Hencky, fluid, volume; fluid and
 // Sigma plasticity).  Without it the kernel handles fixed-corotated and
 // Neo-Hookean with von Mises / Drucker-Prager only, and its register
 // allocation is not shared with the rarer models.
-template <int MODE, int SCAT, int TPB, bool XM>
+template <int MODE, int SCAT, int TPB, bool XM, bool DB>
 __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int spar) {
     extern __shared__ float4 smem_raw[];
     SubstepSmem<TPB> &S = *reinterpret_cast<SubstepSmem<TPB> *>(smem_raw);
     constexpr bool GATHER = MODE != MODE_P2G;
     constexpr bool SCATTER = MODE != MODE_G2P;
-    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    if (DB && blockIdx.x == 0 && threadIdx.x == 0) {
+        // counters this kernel does not read and the next launch starts from:
+        // the activation count of the gather buffer (activated again next)
+        // and the work items of the binning made now
+        D.ctr[CTR_N_ACTIVE + gpar] = 0;
+        D.ctr[CTR_D_CH + spar] = 0;
+    }
+    const unsigned n_chunks = min(D.ctr[D.chunk_ctr], D.chunk_ctr == CTR_N_CHUNKS ? D.max_chunks : D.max_chunks_d);
     const unsigned ep_g = GATHER ? D.ctr[CTR_EPOCH_OF + gpar] : 0u;
     const unsigned ep_s = SCATTER ? D.ctr[CTR_EPOCH_OF + spar] : 0u;
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
@@ -712,7 +846,21 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
                 sr[3] = make_float4(Ad[4], Ad[5], Ad[6], Ad[7]);
                 sr[4] = make_float4(Ad[8], 0.f, 0.f, 0.f);
             }
-            if (MODE != MODE_P2G) bin_end(D, ticket, p);
+            if (DB) {
+                // pool slot of the new block in the scatter buffer: one of the
+                // chunk block's 27 neighbours (a particle moves at most a cell)
+                float fq;
+                const int d0 = (base_cell_q(q[0], D, fq) >> 2) - bx + 1, d1 = (base_cell_q(q[1], D, fq) >> 2) - by + 1,
+                          d2 = (base_cell_q(q[2], D, fq) >> 2) - bz + 1;
+                const bool near = (unsigned)d0 < 3u && (unsigned)d1 < 3u && (unsigned)d2 < 3u;
+                // beyond the neighbourhood (a broken grouping, already reported)
+                // the page table is read, as k_between reads it for the block
+                const int slot = near ? S.slot_s[kc & 1][(d0 * 3 + d1) * 3 + d2]
+                                      : (D.page_epoch[spar][key] == ep_s ? D.page[spar][key] : -1);
+                bin_end_direct(D, ticket, p, slot, spar);
+            } else if (MODE != MODE_P2G) {
+                bin_end(D, ticket, p);
+            }
             }
         }
 
@@ -961,11 +1109,18 @@ void launch_plan(const Dev &D, int bump_mask, cudaStream_t st) { k_plan<<<1, 102
 void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st) {
     k_prepare<<<grid, 256, 0, st>>>(D, upd_par, act_par, do_sort, keep_momentum);
 }
-template <int MODE, int SCAT, int TPB, bool XM>
+template <int MODE, int SCAT, int TPB, bool XM, bool DB = false>
 static void launch_sub(const Dev &D, int gpar, int spar, int grid, cudaStream_t st) {
-    k_substep<MODE, SCAT, TPB, XM><<<grid, TPB, sizeof(SubstepSmem<TPB>), st>>>(D, gpar, spar);
+    k_substep<MODE, SCAT, TPB, XM, DB><<<grid, TPB, sizeof(SubstepSmem<TPB>), st>>>(D, gpar, spar);
 }
-template <int TPB> static void launch_tpb(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st) {
+template <int TPB>
+static void launch_tpb(const Dev &D, int mode, int gpar, int spar, int grid, bool direct, cudaStream_t st) {
+    if (direct && mode == MODE_FUSED) {   // direct binning: scatter strategies 1 and 2
+        if (D.xm) launch_sub<MODE_FUSED, 1, TPB, true, true>(D, gpar, spar, grid, st);
+        else if (D.scatter == 2) launch_sub<MODE_FUSED, 2, TPB, false, true>(D, gpar, spar, grid, st);
+        else launch_sub<MODE_FUSED, 1, TPB, false, true>(D, gpar, spar, grid, st);
+        return;
+    }
     if (D.xm) {   // further models: the shared-memory fixed-point scatter only
         if (mode == MODE_G2P) launch_sub<MODE_G2P, 2, TPB, true>(D, gpar, spar, grid, st);
         else if (mode == MODE_P2G) launch_sub<MODE_P2G, 1, TPB, true>(D, gpar, spar, grid, st);
@@ -984,9 +1139,12 @@ template <int TPB> static void launch_tpb(const Dev &D, int mode, int gpar, int 
     else launch_sub<MODE_FUSED, 2, TPB, false>(D, gpar, spar, grid, st);
 }
 // the chunk size selects the CTA size: chunks of <= 64 particles run 64-thread CTAs
-void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st) {
-    if (D.chunk <= 64) launch_tpb<64>(D, mode, gpar, spar, grid, st);
-    else launch_tpb<128>(D, mode, gpar, spar, grid, st);
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, bool direct, cudaStream_t st) {
+    if (D.chunk <= 64) launch_tpb<64>(D, mode, gpar, spar, grid, direct, st);
+    else launch_tpb<128>(D, mode, gpar, spar, grid, direct, st);
+}
+void launch_between(const Dev &D, int upd, int act, int grid, cudaStream_t st) {
+    k_between<<<grid, 256, 0, st>>>(D, upd, act);
 }
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st) {
     k_export<<<grid_for(D.n, 256), 256, 0, st>>>(D, x, v, C, F);
@@ -996,9 +1154,13 @@ void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cu
 }
 template <int MODE, int SCAT, int TPB, bool XM> static int occ_of() {
     int nb = 0;
-    cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB, XM, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(SubstepSmem<TPB>));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT, TPB, XM>, TPB, sizeof(SubstepSmem<TPB>));
+    if constexpr (MODE == MODE_FUSED && SCAT != 0)   // its direct-binning variant
+        cudaFuncSetAttribute(k_substep<MODE, SCAT, TPB, XM, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(SubstepSmem<TPB>));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_substep<MODE, SCAT, TPB, XM, false>, TPB,
+                                                  sizeof(SubstepSmem<TPB>));
     return nb;
 }
 template <int TPB> static int occ_tpb(int mode, int scatter, bool xm) {

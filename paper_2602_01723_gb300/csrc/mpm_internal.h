@@ -48,7 +48,11 @@ void launch_load(const Dev &D, const LoadArgs &a, cudaStream_t st);
 void launch_bin(const Dev &D, cudaStream_t st);
 void launch_plan(const Dev &D, int bump_mask, cudaStream_t st);
 void launch_prepare(const Dev &D, int upd_par, int act_par, int do_sort, int keep_momentum, int grid, cudaStream_t st);
-void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, cudaStream_t st);
+// direct: the fused mode bins straight into the scatter buffer's lists
+void launch_substep(const Dev &D, int mode, int gpar, int spar, int grid, bool direct, cudaStream_t st);
+// between two direct-binning substeps: grid update of upd, work items of its
+// binning, activation of act (see k_between)
+void launch_between(const Dev &D, int upd, int act, int grid, cudaStream_t st);
 void launch_export(const Dev &D, float *x, float *v, float *C, float *F, cudaStream_t st);
 void launch_grid_dense(const Dev &D, int par, int which, float *m, float *mv, cudaStream_t st);
 int substep_occupancy(int mode, int scatter, int chunk, bool xm);
@@ -153,6 +157,10 @@ struct mpm_ctx {
     long long graph_key = -1;     // (n, buffer generation) the graph was captured for
     long long generation = 0;     // bumped whenever a device buffer the kernels use is reallocated
     bool bins_pending = false;    // a binning (counts / occupied list) awaits its plan
+    // direct binning of the steady-state forward substeps: its lists are
+    // sized at each load (outside a capture) from the load's binning
+    bool direct_ready = false;
+    size_t slist_alloc = 0, ovf_alloc = 0, chunksd_alloc = 0, occd_alloc = 0;   // elements per buffer
     // BGDO key frames (records of the whole particle set) and stage-2 scratch
     float4 *snap[MPM_MAX_SNAPSHOTS] = {};
     long long snap_n[MPM_MAX_SNAPSHOTS] = {};     // particle count at the snapshot (0: empty)
@@ -173,7 +181,10 @@ namespace mpm {
 void L_plan(mpm_ctx *ctx, int bump_mask, cudaStream_t st);
 // grid update of upd_par, activation of act_par, sorted index (see k_prepare)
 void L_prepare(mpm_ctx *ctx, int upd_par, int act_par, int do_sort, cudaStream_t st, int keep_momentum = 0);
-void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st);
+// direct: bin straight into the scatter buffer's lists (fused mode); in_par
+// >= 0: read the work items of the direct binning into buffer in_par
+void L_substep(mpm_ctx *ctx, int mode, int gpar, int spar, cudaStream_t st, bool direct = false, int in_par = -1);
+void L_between(mpm_ctx *ctx, int upd, int act, cudaStream_t st);
 void L_bin(mpm_ctx *ctx, cudaStream_t st);
 void launch_bgdo_accum(const Dev &D, const float4 *key, const float4 *post, int first, float inv_k,
                        float delta_target, float w, float *G, float *g_tau, float *delta, cudaStream_t st);
