@@ -9,6 +9,11 @@
 // grid velocity at x_s, updates x, v, C, F (and applies the return map),
 // evaluates the stress of the new F and scatters mass and momentum at x_{s+1}
 // into a shared-memory tile, then bins the particle for the next substep.
+// Without a tape the forward bins directly from substep 1 on: the fused
+// kernel writes each particle's index into the list of its new block (at
+// the block's pool slot), and k_between (grid update, chunks from the list
+// counts, activation of the next buffer) replaces plan and sort:
+//   ... -> [k_between(s) -> G2P(s) fused with P2G(s+1) + list write] -> ...
 #include "mpm_dev.cuh"
 #include "mpm_internal.h"
 #include "mpm_math.cuh"

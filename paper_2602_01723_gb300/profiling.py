@@ -31,13 +31,39 @@ TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SOURCES = ("mpm_forward.cu", "mpm_math.cuh", "mpm_dev.cuh")
 
 
+def strip_comments(src: str) -> str:
+    """C++ source without its // and /* */ comments (string and character
+    literals kept), so that a comment edit leaves the hash unchanged."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return "".join(out)
+
+
 def source_hash() -> str:
-    """sha256 over the sources of the substep kernel's device code."""
+    """sha256 over the sources of the substep kernel's device code, comments
+    stripped and runs of white space taken as one space."""
     h = hashlib.sha256()
     csrc = os.path.join(HERE, "csrc")
     for f in KERNEL_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + b"\0" + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + b"\0" + " ".join(strip_comments(fh.read()).split()).encode())
     return h.hexdigest()[:16]
 
 
