@@ -180,4 +180,21 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Claims n consecutive indices of *ctr for each lane (n = 0: none) with one
+// atomic per warp; returns the lane's first index.  Every lane of the warp
+// must call it together (a warp-uniform loop).
+__device__ __forceinline__ unsigned warp_claim(unsigned *ctr, unsigned n) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (unsigned)o) incl += u;
+    }
+    const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+    unsigned base = 0;
+    if (lane == 31 && total) base = atomicAdd(ctr, total);
+    return __shfl_sync(0xffffffffu, base, 31) + incl - n;
+}
+
 }  // namespace mpm

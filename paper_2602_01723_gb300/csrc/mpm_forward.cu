@@ -251,6 +251,42 @@ __global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_mask) {
     }
 }
 
+// Activation of buffer par around the listed blocks under epoch ep: each
+// neighbour (3^3 around a block) inside the grid takes the epoch and, the
+// first time, a pool slot.  Warp-uniform loop: the slot counter is claimed
+// once per warp, not once per block.
+__device__ __forceinline__ void activate_around(const Dev &D, const unsigned *blocks, unsigned nblocks, int par,
+                                                unsigned ep) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned items = nblocks * 27u;
+    for (unsigned w0 = tid - lane; w0 < items; w0 += stride) {
+        const unsigned i = w0 + lane;
+        unsigned nk = 0;
+        bool fresh = false;
+        if (i < items) {
+            const unsigned b = i / 27u, o = i - b * 27u;
+            int inst, bx, by, bz;
+            key_coords(D, blocks[b], inst, bx, by, bz);
+            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
+            if (nx >= 0 && ny >= 0 && nz >= 0 && nx < D.NB[0] && ny < D.NB[1] && nz < D.NB[2]) {
+                nk = block_key(D, inst, nx, ny, nz);
+                fresh = atomicMax(&D.page_epoch[par][nk], ep) != ep;
+            }
+        }
+        const unsigned slot = warp_claim(&D.ctr[CTR_N_ACTIVE + par], fresh ? 1u : 0u);
+        if (fresh) {
+            if (slot < D.max_active) {
+                D.page[par][nk] = (int)slot;
+                D.active[par][slot] = nk;
+            } else {
+                D.page[par][nk] = -1;
+                set_err(D, ERRB_CAPACITY);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // one launch between two substep kernels, three independent parts:
 //   * the grid update (App. A) of buffer upd_par: v = mv/m + dt g for m > 0,
@@ -298,29 +334,7 @@ __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep
             if (!keep_momentum) D.gmv[upd_par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (act_par >= 0) {
-        const unsigned ep = D.ctr[CTR_EPOCH_OF + act_par];
-        const unsigned items = D.ctr[CTR_N_PLAN] * 27u;
-        for (unsigned i = tid; i < items; i += stride) {
-            const unsigned b = i / 27u, o = i - b * 27u;
-            int inst, bx, by, bz;
-            key_coords(D, D.plan[b], inst, bx, by, bz);
-            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
-            if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
-            const unsigned nk = block_key(D, inst, nx, ny, nz);
-            const unsigned old = atomicMax(&D.page_epoch[act_par][nk], ep);
-            if (old != ep) {
-                const unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + act_par], 1u);
-                if (slot < D.max_active) {
-                    D.page[act_par][nk] = (int)slot;
-                    D.active[act_par][slot] = nk;
-                } else {
-                    D.page[act_par][nk] = -1;
-                    set_err(D, ERRB_CAPACITY);
-                }
-            }
-        }
-    }
+    if (act_par >= 0) activate_around(D, D.plan, D.ctr[CTR_N_PLAN], act_par, D.ctr[CTR_EPOCH_OF + act_par]);
     if (do_sort)
         for (unsigned p = tid; p < (unsigned)D.n; p += stride) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
 }
@@ -374,16 +388,22 @@ __global__ void k_between(Dev D, int upd, int act) {
             D.gmv[upd][i] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    // work items: the lists of the occupied blocks
-    for (unsigned i = tid; i < nocc; i += stride) {
-        const unsigned key = D.occd[upd][i];
-        const unsigned cnt = D.bcount[key];
-        D.bcount[key] = 0;
-        const int sl = D.page_epoch[upd][key] == ep_upd ? D.page[upd][key] : -1;
-        const unsigned main = (sl >= 0 && (unsigned)sl < D.slist_blocks) ? min(cnt, D.slist_cap) : 0u;
+    // work items: the lists of the occupied blocks (warp-uniform loops: the
+    // counters are claimed once per warp)
+    const unsigned lane = threadIdx.x & 31u;
+    for (unsigned w0 = tid - lane; w0 < nocc; w0 += stride) {
+        const unsigned i = w0 + lane;
+        unsigned key = 0, main = 0;
+        int sl = -1;
+        if (i < nocc) {
+            key = D.occd[upd][i];
+            const unsigned cnt = D.bcount[key];
+            D.bcount[key] = 0;
+            sl = D.page_epoch[upd][key] == ep_upd ? D.page[upd][key] : -1;
+            main = (sl >= 0 && (unsigned)sl < D.slist_blocks) ? min(cnt, D.slist_cap) : 0u;
+        }
         const unsigned nch = (main + CH - 1) / CH;
-        if (nch == 0) continue;
-        const unsigned c0 = atomicAdd(&D.ctr[CTR_D_CH + upd], nch);
+        const unsigned c0 = warp_claim(&D.ctr[CTR_D_CH + upd], nch);
         for (unsigned j = 0; j < nch; ++j) {
             if (c0 + j < D.max_chunks_d)
                 D.chunksd[upd][c0 + j] = make_int4((int)key, (int)((unsigned)sl * D.slist_cap + j * CH),
@@ -393,34 +413,15 @@ __global__ void k_between(Dev D, int upd, int act) {
         }
     }
     // one work item per overflow entry (list 1)
-    for (unsigned o = tid; o < novf; o += stride) {
-        const unsigned c = atomicAdd(&D.ctr[CTR_D_CH + upd], 1u);
+    for (unsigned w0 = tid - lane; w0 < novf; w0 += stride) {
+        const unsigned o = w0 + lane;
+        const unsigned c = warp_claim(&D.ctr[CTR_D_CH + upd], o < novf ? 1u : 0u);
+        if (o >= novf) continue;
         if (c < D.max_chunks_d) D.chunksd[upd][c] = make_int4((int)D.ovf[upd][2 * o + 1], (int)(2 * o), 1, 1);
         else set_err(D, ERRB_CAPACITY);
     }
     // activation of act around the occupied blocks
-    if (act >= 0) {
-        const unsigned items = nocc * 27u;
-        for (unsigned i = tid; i < items; i += stride) {
-            const unsigned b = i / 27u, o = i - b * 27u;
-            int inst, bx, by, bz;
-            key_coords(D, D.occd[upd][b], inst, bx, by, bz);
-            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
-            if (nx < 0 || ny < 0 || nz < 0 || nx >= D.NB[0] || ny >= D.NB[1] || nz >= D.NB[2]) continue;
-            const unsigned nk = block_key(D, inst, nx, ny, nz);
-            const unsigned old = atomicMax(&D.page_epoch[act][nk], ep_new);
-            if (old != ep_new) {
-                const unsigned slot = atomicAdd(&D.ctr[CTR_N_ACTIVE + act], 1u);
-                if (slot < D.max_active) {
-                    D.page[act][nk] = (int)slot;
-                    D.active[act][slot] = nk;
-                } else {
-                    D.page[act][nk] = -1;
-                    set_err(D, ERRB_CAPACITY);
-                }
-            }
-        }
-    }
+    if (act >= 0) activate_around(D, D.occd[upd], nocc, act, ep_new);
 }
 
 // ---------------------------------------------------------------------------
