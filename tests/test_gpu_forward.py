@@ -104,7 +104,13 @@ def test_one_substep_all_models(orc, sim_mod):
     v, C, F = stressed_state(sc, fs=0.1)
     got, ref = substep_compare(orc, sim_mod, sc, v, C, F)
     vs = np.abs(ref["v"]).max()
-    assert np.abs(got["v"] - ref["v"]).max() < 1e-5 * vs
+    # The grid mass and momentum of this state are held to 1e-5 (the
+    # test_p2g_grid_same_state cases); a particle's new velocity also divides
+    # by each node's mass, which amplifies the relative error of light nodes.
+    # The float reductions into shared nodes run in no fixed order: over 20
+    # runs the error was 4.8e-6 .. 1.01e-5 of |v|max and two GPU runs differed
+    # by up to 1.0e-5, hence 2e-5.
+    assert np.abs(got["v"] - ref["v"]).max() < 2e-5 * vs
     # x is returned as FP32 world coordinates: near 0.5 on this 32^3 grid one
     # rounding of the output is up to 0.95e-6 dx by itself; the fixed-point
     # state adds at most 2^-23 of a cell
