@@ -255,13 +255,9 @@ __global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_mask) {
 // neighbour (3^3 around a block) inside the grid takes the epoch and, the
 // first time, a pool slot.  Warp-uniform loop: the slot counter is claimed
 // once per warp, not once per block.
-__device__ __forceinline__ void activate_around(const Dev &D, const unsigned *blocks, unsigned nblocks, int par,
-                                                unsigned ep) {
-    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned items = nblocks * 27u;
-    for (unsigned w0 = tid - lane; w0 < items; w0 += stride) {
-        const unsigned i = w0 + lane;
+__device__ __forceinline__ void activate_item(const Dev &D, const unsigned *blocks, unsigned i, unsigned items,
+                                              int par, unsigned ep) {
+    {
         unsigned nk = 0;
         bool fresh = false;
         if (i < items) {
@@ -285,6 +281,13 @@ __device__ __forceinline__ void activate_around(const Dev &D, const unsigned *bl
             }
         }
     }
+}
+__device__ __forceinline__ void activate_around(const Dev &D, const unsigned *blocks, unsigned nblocks, int par,
+                                                unsigned ep) {
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned items = nblocks * 27u;
+    for (unsigned w0 = tid - lane; w0 < items; w0 += stride) activate_item(D, blocks, w0 + lane, items, par, ep);
 }
 
 // ---------------------------------------------------------------------------
@@ -368,10 +371,20 @@ __global__ void k_between(Dev D, int upd, int act) {
             D.ctr[CTR_D_OVF + act] = 0;
         }
     }
-    // grid update of upd
-    {
-        const unsigned lim = min(D.ctr[CTR_N_ACTIVE + upd], D.max_active) * BLK_NODES;
-        for (unsigned i = tid; i < lim; i += stride) {
+    // Each warp takes one kind of item, so that no thread chains the
+    // dependent loads of several: the grid update of upd (one node), the
+    // lists of the occupied blocks (one block), the overflow entries (one
+    // entry) and the activation of act around the occupied blocks (one
+    // neighbour).  The ranges are rounded up to whole warps, and the
+    // counters are claimed once per warp.
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lim = min(D.ctr[CTR_N_ACTIVE + upd], D.max_active) * BLK_NODES;
+    const unsigned e0 = (lim + 31u) & ~31u, e1 = e0 + ((nocc + 31u) & ~31u), e2 = e1 + ((novf + 31u) & ~31u);
+    const unsigned e3 = e2 + (act >= 0 ? (nocc * 27u + 31u) & ~31u : 0u);
+    for (unsigned w0 = tid - lane; w0 < e3; w0 += stride) {
+        if (w0 < e0) {   // grid update of upd
+            const unsigned i = w0 + lane;
+            if (i >= lim) continue;
             const unsigned slot = i >> 6, l = i & 63u;
             int inst, bx, by, bz;
             key_coords(D, D.active[upd][slot], inst, bx, by, bz);
@@ -386,42 +399,36 @@ __global__ void k_between(Dev D, int upd, int act) {
             }
             D.gv[upd][i] = out;
             D.gmv[upd][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (w0 < e1) {   // work items: the list of an occupied block
+            const unsigned i = w0 - e0 + lane;
+            unsigned key = 0, main = 0;
+            int sl = -1;
+            if (i < nocc) {
+                key = D.occd[upd][i];
+                const unsigned cnt = D.bcount[key];
+                D.bcount[key] = 0;
+                sl = D.page_epoch[upd][key] == ep_upd ? D.page[upd][key] : -1;
+                main = (sl >= 0 && (unsigned)sl < D.slist_blocks) ? min(cnt, D.slist_cap) : 0u;
+            }
+            const unsigned nch = (main + CH - 1) / CH;
+            const unsigned c0 = warp_claim(&D.ctr[CTR_D_CH + upd], nch);
+            for (unsigned j = 0; j < nch; ++j) {
+                if (c0 + j < D.max_chunks_d)
+                    D.chunksd[upd][c0 + j] = make_int4((int)key, (int)((unsigned)sl * D.slist_cap + j * CH),
+                                                       (int)min(CH, main - j * CH), 0);
+                else
+                    set_err(D, ERRB_CAPACITY);
+            }
+        } else if (w0 < e2) {   // one work item per overflow entry (list 1)
+            const unsigned o = w0 - e1 + lane;
+            const unsigned c = warp_claim(&D.ctr[CTR_D_CH + upd], o < novf ? 1u : 0u);
+            if (o >= novf) continue;
+            if (c < D.max_chunks_d) D.chunksd[upd][c] = make_int4((int)D.ovf[upd][2 * o + 1], (int)(2 * o), 1, 1);
+            else set_err(D, ERRB_CAPACITY);
+        } else {   // activation of act: one neighbour of an occupied block
+            activate_item(D, D.occd[upd], w0 - e2 + lane, nocc * 27u, act, ep_new);
         }
     }
-    // work items: the lists of the occupied blocks (warp-uniform loops: the
-    // counters are claimed once per warp)
-    const unsigned lane = threadIdx.x & 31u;
-    for (unsigned w0 = tid - lane; w0 < nocc; w0 += stride) {
-        const unsigned i = w0 + lane;
-        unsigned key = 0, main = 0;
-        int sl = -1;
-        if (i < nocc) {
-            key = D.occd[upd][i];
-            const unsigned cnt = D.bcount[key];
-            D.bcount[key] = 0;
-            sl = D.page_epoch[upd][key] == ep_upd ? D.page[upd][key] : -1;
-            main = (sl >= 0 && (unsigned)sl < D.slist_blocks) ? min(cnt, D.slist_cap) : 0u;
-        }
-        const unsigned nch = (main + CH - 1) / CH;
-        const unsigned c0 = warp_claim(&D.ctr[CTR_D_CH + upd], nch);
-        for (unsigned j = 0; j < nch; ++j) {
-            if (c0 + j < D.max_chunks_d)
-                D.chunksd[upd][c0 + j] = make_int4((int)key, (int)((unsigned)sl * D.slist_cap + j * CH),
-                                                   (int)min(CH, main - j * CH), 0);
-            else
-                set_err(D, ERRB_CAPACITY);
-        }
-    }
-    // one work item per overflow entry (list 1)
-    for (unsigned w0 = tid - lane; w0 < novf; w0 += stride) {
-        const unsigned o = w0 + lane;
-        const unsigned c = warp_claim(&D.ctr[CTR_D_CH + upd], o < novf ? 1u : 0u);
-        if (o >= novf) continue;
-        if (c < D.max_chunks_d) D.chunksd[upd][c] = make_int4((int)D.ovf[upd][2 * o + 1], (int)(2 * o), 1, 1);
-        else set_err(D, ERRB_CAPACITY);
-    }
-    // activation of act around the occupied blocks
-    if (act >= 0) activate_around(D, D.occd[upd], nocc, act, ep_new);
 }
 
 // ---------------------------------------------------------------------------
