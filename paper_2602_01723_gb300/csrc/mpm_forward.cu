@@ -251,43 +251,34 @@ __global__ void __launch_bounds__(1024) k_plan(Dev D, int bump_mask) {
     }
 }
 
-// Activation of buffer par around the listed blocks under epoch ep: each
-// neighbour (3^3 around a block) inside the grid takes the epoch and, the
-// first time, a pool slot.  Warp-uniform loop: the slot counter is claimed
-// once per warp, not once per block.
+// Activation of buffer par around the listed blocks under epoch ep, item i
+// of items = 27 x blocks: the neighbour i % 27 of block i / 27, if inside the
+// grid, takes the epoch and, the first time, a pool slot.  All lanes of a
+// warp call it together (the slot counter is claimed once per warp).
 __device__ __forceinline__ void activate_item(const Dev &D, const unsigned *blocks, unsigned i, unsigned items,
                                               int par, unsigned ep) {
-    {
-        unsigned nk = 0;
-        bool fresh = false;
-        if (i < items) {
-            const unsigned b = i / 27u, o = i - b * 27u;
-            int inst, bx, by, bz;
-            key_coords(D, blocks[b], inst, bx, by, bz);
-            const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
-            if (nx >= 0 && ny >= 0 && nz >= 0 && nx < D.NB[0] && ny < D.NB[1] && nz < D.NB[2]) {
-                nk = block_key(D, inst, nx, ny, nz);
-                fresh = atomicMax(&D.page_epoch[par][nk], ep) != ep;
-            }
-        }
-        const unsigned slot = warp_claim(&D.ctr[CTR_N_ACTIVE + par], fresh ? 1u : 0u);
-        if (fresh) {
-            if (slot < D.max_active) {
-                D.page[par][nk] = (int)slot;
-                D.active[par][slot] = nk;
-            } else {
-                D.page[par][nk] = -1;
-                set_err(D, ERRB_CAPACITY);
-            }
+    unsigned nk = 0;
+    bool fresh = false;
+    if (i < items) {
+        const unsigned b = i / 27u, o = i - b * 27u;
+        int inst, bx, by, bz;
+        key_coords(D, blocks[b], inst, bx, by, bz);
+        const int nx = bx + (int)(o / 9u) - 1, ny = by + (int)((o / 3u) % 3u) - 1, nz = bz + (int)(o % 3u) - 1;
+        if (nx >= 0 && ny >= 0 && nz >= 0 && nx < D.NB[0] && ny < D.NB[1] && nz < D.NB[2]) {
+            nk = block_key(D, inst, nx, ny, nz);
+            fresh = atomicMax(&D.page_epoch[par][nk], ep) != ep;
         }
     }
-}
-__device__ __forceinline__ void activate_around(const Dev &D, const unsigned *blocks, unsigned nblocks, int par,
-                                                unsigned ep) {
-    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    const unsigned lane = threadIdx.x & 31u;
-    const unsigned items = nblocks * 27u;
-    for (unsigned w0 = tid - lane; w0 < items; w0 += stride) activate_item(D, blocks, w0 + lane, items, par, ep);
+    const unsigned slot = warp_claim(&D.ctr[CTR_N_ACTIVE + par], fresh ? 1u : 0u);
+    if (fresh) {
+        if (slot < D.max_active) {
+            D.page[par][nk] = (int)slot;
+            D.active[par][slot] = nk;
+        } else {
+            D.page[par][nk] = -1;
+            set_err(D, ERRB_CAPACITY);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -318,9 +309,19 @@ __device__ __forceinline__ void apply_walls(const Dev &D, int I, int J, int K, f
 
 __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep_momentum) {
     const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
-    if (upd_par >= 0) {
-        const unsigned lim = min(D.ctr[CTR_N_ACTIVE + upd_par], D.max_active) * BLK_NODES;
-        for (unsigned i = tid; i < lim; i += stride) {
+    // each warp takes one kind of item (a grid node, an activation neighbour,
+    // a particle to sort), ranges rounded up to whole warps: no thread chains
+    // the dependent loads of several parts
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lim = upd_par >= 0 ? min(D.ctr[CTR_N_ACTIVE + upd_par], D.max_active) * BLK_NODES : 0u;
+    const unsigned n_act = act_par >= 0 ? D.ctr[CTR_N_PLAN] * 27u : 0u;
+    const unsigned n_sort = do_sort ? (unsigned)D.n : 0u;
+    const unsigned e0 = (lim + 31u) & ~31u, e1 = e0 + ((n_act + 31u) & ~31u), e2 = e1 + ((n_sort + 31u) & ~31u);
+    const unsigned ep_act = act_par >= 0 ? D.ctr[CTR_EPOCH_OF + act_par] : 0u;
+    for (unsigned w0 = tid - lane; w0 < e2; w0 += stride) {
+        if (w0 < e0) {   // grid update of upd_par
+            const unsigned i = w0 + lane;
+            if (i >= lim) continue;
             const unsigned slot = i >> 6, l = i & 63u;
             int inst, bx, by, bz;
             key_coords(D, D.active[upd_par][slot], inst, bx, by, bz);
@@ -335,11 +336,13 @@ __global__ void k_prepare(Dev D, int upd_par, int act_par, int do_sort, int keep
             }
             D.gv[upd_par][i] = out;
             if (!keep_momentum) D.gmv[upd_par][i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (w0 < e1) {   // activation of act_par: one neighbour of a planned block
+            activate_item(D, D.plan, w0 - e0 + lane, n_act, act_par, ep_act);
+        } else {   // the sorted index
+            const unsigned p = w0 - e1 + lane;
+            if (p < n_sort) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
         }
     }
-    if (act_par >= 0) activate_around(D, D.plan, D.ctr[CTR_N_PLAN], act_par, D.ctr[CTR_EPOCH_OF + act_par]);
-    if (do_sort)
-        for (unsigned p = tid; p < (unsigned)D.n; p += stride) D.sorted[D.bstart[D.key[p]] + D.rank[p]] = p;
 }
 
 // ---------------------------------------------------------------------------
