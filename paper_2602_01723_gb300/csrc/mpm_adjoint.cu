@@ -429,6 +429,17 @@ __device__ __forceinline__ void a_cp4(void *dst, const void *src) {
 __device__ __forceinline__ void a_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void a_wait() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// the descriptors of this CTA's first two chunks (thread 0), read alongside
+// the chunk count: any index within the array's capacity is readable, and
+// one beyond the count is not used
+__device__ __forceinline__ void first_descriptors(const Dev &D, int4 &cd0, int4 &cd1) {
+    cd0 = cd1 = make_int4(0, 0, 0, 0);
+    if (threadIdx.x == 0) {
+        if (blockIdx.x < D.max_chunks) cd0 = D.chunks[blockIdx.x];
+        if (blockIdx.x + gridDim.x < D.max_chunks) cd1 = D.chunks[blockIdx.x + gridDim.x];
+    }
+}
+
 // level 2 of a chunk: sorted indices and the page words of its 8 tile blocks
 template <typename SM>
 __device__ __forceinline__ void adj_stage2(const Dev &D, SM &S, int4 ch, unsigned ep) {
@@ -490,7 +501,9 @@ template <int MS>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 *__restrict__ ain, float4 *aout,
                                                          float4 *gpar, float4 *gbar) {
     __shared__ AdjG2PSmem S;
-    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    int4 cd0, cd1;
+    first_descriptors(D, cd0, cd1);
+    const unsigned n_chunks = min(D.ctr[CTR_N_CHUNKS], D.max_chunks);
     const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
     const float c4 = 4.f * inv_dx * inv_dx;
@@ -499,8 +512,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_g2p(Dev D, const float4 
     if (c >= n_chunks) return;
     // prologue: descriptors of c and c + G, levels 2 and 3 of chunk c
     if (tid == 0) {
-        S.cd[0] = D.chunks[c];
-        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+        S.cd[0] = cd0;
+        if (c + gridDim.x < n_chunks) S.cd[1] = cd1;
     }
     for (int t = tid; t < 3 * GT3P; t += ADJ_THREADS) S.t[t] = 0;
     __syncthreads();
@@ -840,15 +853,17 @@ __device__ __forceinline__ void adj_p2g_stage3(const Dev &D, AdjP2GSmem &S, int4
 template <int EL>
 __global__ void __launch_bounds__(ADJ_THREADS, 3) k_adj_p2g(Dev D, float4 *aout, float4 *gpar, const float4 *gbar) {
     __shared__ AdjP2GSmem S;
-    const unsigned n_chunks = D.ctr[CTR_N_CHUNKS];
+    int4 cd0, cd1;
+    first_descriptors(D, cd0, cd1);
+    const unsigned n_chunks = min(D.ctr[CTR_N_CHUNKS], D.max_chunks);
     const unsigned ep = D.ctr[CTR_EPOCH_OF + 0];
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
     const int tid = threadIdx.x;
     unsigned c = blockIdx.x;
     if (c >= n_chunks) return;
     if (tid == 0) {
-        S.cd[0] = D.chunks[c];
-        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+        S.cd[0] = cd0;
+        if (c + gridDim.x < n_chunks) S.cd[1] = cd1;
     }
     __syncthreads();
     adj_stage2(D, S, S.cd[0], ep);

@@ -609,7 +609,16 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
         D.ctr[CTR_N_ACTIVE + gpar] = 0;
         D.ctr[CTR_D_CH + spar] = 0;
     }
-    const unsigned n_chunks = min(D.ctr[D.chunk_ctr], D.chunk_ctr == CTR_N_CHUNKS ? D.max_chunks : D.max_chunks_d);
+    // the first two descriptors are read alongside the counters: any index
+    // within the array's capacity is readable, and one beyond the count is
+    // dropped below
+    const unsigned cap_ch = D.chunk_ctr == CTR_N_CHUNKS ? D.max_chunks : D.max_chunks_d;
+    int4 cd0 = make_int4(0, 0, 0, 0), cd1 = cd0;
+    if (threadIdx.x == 0) {
+        if (blockIdx.x < cap_ch) cd0 = D.chunks[blockIdx.x];
+        if (blockIdx.x + gridDim.x < cap_ch) cd1 = D.chunks[blockIdx.x + gridDim.x];
+    }
+    const unsigned n_chunks = min(D.ctr[D.chunk_ctr], cap_ch);
     const unsigned ep_g = GATHER ? D.ctr[CTR_EPOCH_OF + gpar] : 0u;
     const unsigned ep_s = SCATTER ? D.ctr[CTR_EPOCH_OF + spar] : 0u;
     const float dx = D.dx, inv_dx = D.inv_dx, dt = D.dt;
@@ -619,8 +628,8 @@ __global__ void __launch_bounds__(TPB, 512 / TPB) k_substep(Dev D, int gpar, int
 
     // prologue: descriptors of chunks c and c + G; levels 2 and 3 of chunk c
     if (tid == 0) {
-        S.cd[0] = D.chunks[c];
-        if (c + gridDim.x < n_chunks) S.cd[1] = D.chunks[c + gridDim.x];
+        S.cd[0] = cd0;
+        if (c + gridDim.x < n_chunks) S.cd[1] = cd1;
     }
     if (SCATTER && SCAT != 2)
         for (int t = tid; t < 4 * ST3P; t += T) S.t.i[t] = 0;
