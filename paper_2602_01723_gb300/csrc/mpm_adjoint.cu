@@ -1750,6 +1750,9 @@ extern "C" MPM_API mpm_status mpm_backward(mpm_ctx *ctx, int32_t n_frames, const
                cudaSuccess;
     };
     for (int attempt = 0;; ++attempt) {
+    // the slot-overflow flag of this attempt (a rerun may keep the tape)
+    if (use_gt && cudaMemsetAsync(gt_over(ctx), 0, sizeof(unsigned), st) != cudaSuccess)
+        return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
     if (cudaMemsetAsync(A.adj[0], 0, n * ADJ_F4 * sizeof(float4), st) != cudaSuccess ||
         cudaMemsetAsync(A.gpar, 0, n * sizeof(float4), st) != cudaSuccess)
         return ctx_fail(ctx, MPM_ERR_CUDA, "backward set-up copies");
