@@ -1227,7 +1227,8 @@ void free_adjoint(AdjointStore &a) {
     a = AdjointStore();
 }
 
-static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
+// checkpoint slot c, allocated if needed (not inside a stream capture)
+static mpm_status checkpoint_slot(mpm_ctx *ctx, size_t c, cudaStream_t st) {
     AdjointStore &A = ctx->adj;
     const size_t bytes = (size_t)ctx->cap * REC_F4 * sizeof(float4);
     if (A.ckpt.size() <= c) A.ckpt.resize(c + 1, nullptr);
@@ -1244,7 +1245,13 @@ static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
             return ctx_fail(ctx, MPM_ERR_OOM, "checkpoint allocation failed");
         }
     }
-    cudaError_t e = cudaMemcpyAsync(A.ckpt[c], ctx->D.rec, (size_t)ctx->D.n * REC_F4 * sizeof(float4),
+    return MPM_OK;
+}
+
+static mpm_status save_checkpoint(mpm_ctx *ctx, size_t c, cudaStream_t st) {
+    mpm_status s = checkpoint_slot(ctx, c, st);
+    if (s) return s;
+    cudaError_t e = cudaMemcpyAsync(ctx->adj.ckpt[c], ctx->D.rec, (size_t)ctx->D.n * REC_F4 * sizeof(float4),
                                     cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return ctx_fail(ctx, MPM_ERR_CUDA, std::string("checkpoint copy: ") + cudaGetErrorString(e));
     return MPM_OK;
@@ -1260,6 +1267,26 @@ mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st) {
         ctx->adj.ckpt.clear();
     }
     const long long k = ctx->opt.ckpt_every;
+    if (direct_forward(ctx, n_sub)) {
+        // one run; the checkpoints of the states it reaches are copied after
+        // the substeps that complete them
+        if (ctx->recorded % k == 0) {
+            mpm_status s = save_checkpoint(ctx, (size_t)(ctx->recorded / k), st);
+            if (s) return s;
+        }
+        std::vector<StateCopy> copies;
+        for (long long j = k - ctx->recorded % k; j < n_sub; j += k) {
+            const size_t c = (size_t)((ctx->recorded + j) / k);
+            mpm_status s = checkpoint_slot(ctx, c, st);
+            if (s) return s;
+            copies.push_back(StateCopy{(int)j, ctx->adj.ckpt[c]});
+        }
+        ctx->adj.cap = ctx->cap;
+        mpm_status s = run_substeps(ctx, n_sub, st, nullptr, 0, &copies);
+        if (s) return s;
+        ctx->recorded += n_sub;
+        return MPM_OK;
+    }
     int remaining = n_sub;
     while (remaining > 0) {
         if (ctx->recorded % k == 0) {

@@ -336,7 +336,12 @@ static cudaGraphExec_t graph_pair(mpm_ctx *ctx, cudaStream_t st, bool direct) {
 // forward of n substeps from the current state (bins must be valid);
 // leaves the state advanced and binned.  With tape != NULL the records after
 // substep s (s = 0 .. n_sub-1) are also copied to tape + (s+1) * tape_stride.
-mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, size_t tape_stride) {
+bool direct_forward(const mpm_ctx *ctx, int n_sub) {
+    return ctx->direct_ready && ctx->D.scatter != 0 && n_sub > 1;
+}
+
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, size_t tape_stride,
+                        const std::vector<StateCopy> *copies) {
     if (n_sub <= 0) return MPM_OK;
     const size_t rec_bytes = (size_t)ctx->D.n * REC_F4 * sizeof(float4);
     auto tape_copy = [&](int s) -> bool {
@@ -351,24 +356,37 @@ mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape, 
     // 2): the fused substeps place each particle straight into its new
     // block's list, and one k_between launch (no scan, no sort) prepares the
     // next substep.  Substep 0 runs on the plan above.
-    if (!tape && ctx->direct_ready && ctx->D.scatter != 0 && middle > 0) {
+    // The copies are taken after the fused kernel that completes their state;
+    // a graph pair is not replayed across one.
+    if (!tape && direct_forward(ctx, n_sub)) {
+        size_t ci = 0;
+        auto due = [&](int state) { return copies && ci < copies->size() && (*copies)[ci].state == state; };
+        auto copy_after = [&](int state) -> bool {
+            for (; due(state); ++ci)
+                if (cudaMemcpyAsync((*copies)[ci].dst, ctx->D.rec, rec_bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return false;
+            return true;
+        };
         CK(cudaMemsetAsync(ctx->D.ctr + CTR_D_OCC, 0, 6 * sizeof(unsigned), st));
         L_prepare(ctx, 0, 1, 0, st);
         L_substep(ctx, 1, 0, 1, st, true, -1);
-        int s = 1;
-        if (ctx->use_graph && !ctx->trace_on && middle >= 5 && !stream_capturing(st)) {
-            cudaGraphExec_t ex = graph_pair(ctx, st, true);
-            if (ex) {
-                for (; s + 1 < middle; s += 2) {
-                    if (cudaGraphLaunch(ex, st) != cudaSuccess) {
-                        cudaGetLastError();
-                        return fail(ctx, MPM_ERR_CUDA, "graph launch failed");
-                    }
-                    ctx->launches += 4;   // two substeps: between + fused substep each
+        if (!copy_after(1)) return fail(ctx, MPM_ERR_CUDA, "state copy failed");
+        cudaGraphExec_t ex = nullptr;
+        if (ctx->use_graph && !ctx->trace_on && middle >= 5 && !stream_capturing(st)) ex = graph_pair(ctx, st, true);
+        for (int s = 1; s < middle;) {
+            if (ex && (s & 1) && s + 1 < middle && !due(s + 1)) {   // substeps s and s + 1
+                if (cudaGraphLaunch(ex, st) != cudaSuccess) {
+                    cudaGetLastError();
+                    return fail(ctx, MPM_ERR_CUDA, "graph launch failed");
                 }
+                ctx->launches += 4;   // two substeps: between + fused substep each
+                s += 2;
+            } else {
+                middle_direct(ctx, s & 1, st);
+                s += 1;
             }
+            if (!copy_after(s)) return fail(ctx, MPM_ERR_CUDA, "state copy failed");
         }
-        for (; s < middle; ++s) middle_direct(ctx, s & 1, st);
         L_between(ctx, middle & 1, -1, st);              // work items of the last binning
         L_substep(ctx, 2, middle & 1, 0, st, false, middle & 1);
         ctx->bins_pending = true;     // the last substep binned the new positions (for a sort)

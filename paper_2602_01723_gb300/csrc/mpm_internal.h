@@ -196,7 +196,16 @@ void launch_reduce_by_material(const Dev &D, int n_mat, const float *per_particl
 mpm_status ensure_chunks(mpm_ctx *ctx);
 // re-bins the records D.rec points at (after the bins of another state)
 void rebin(mpm_ctx *ctx, cudaStream_t st);
-mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape = nullptr, size_t tape_stride = 0);
+// a copy of the particle records taken once `state` substeps of a run are done
+// (1 <= state < n_sub), in increasing order of state
+struct StateCopy {
+    int state;
+    float4 *dst;
+};
+mpm_status run_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st, float4 *tape = nullptr, size_t tape_stride = 0,
+                        const std::vector<StateCopy> *copies = nullptr);
+// whether run_substeps bins directly for a run of n_sub substeps without a tape
+bool direct_forward(const mpm_ctx *ctx, int n_sub);
 mpm_status record_substeps(mpm_ctx *ctx, int n_sub, cudaStream_t st);
 mpm_status ctx_fail(mpm_ctx *ctx, mpm_status s, const std::string &m);
 mpm_status ctx_check(mpm_ctx *ctx, cudaStream_t st);
